@@ -1,0 +1,111 @@
+"""Seeded synthetic inputs of the paper's workload shapes.
+
+This module holds input recipes only -- grid sizes, bands, option flags and
+random parameter draws -- and none of the likelihood arithmetic.  It is the one
+module that both the GPU library's tests/benchmarks and the CPU oracle's tests
+use, so that both sides see identical inputs.
+
+Shapes follow Sec. II.C / Table I of arXiv:2501.08261 (MBHB, Delta t = 5 s,
+months-long signals, f_min = 1e-4 Hz, band up to 0.02 Hz).
+"""
+import math
+
+import numpy as np
+
+DAY = 86400.0
+
+# Named workloads.  n = number of samples at dt = 5 s; orbit 0 rigid, 1 Keplerian.
+CONFIGS = {
+    # one day, (2,+-2) only, aligned, rigid equal arms, TDI 1.5, p = 31
+    "c1_fp64_1d": dict(dt=5.0, n=17280, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=15,
+                       channel_mask=7, lagrange_order=31, orbit=0, mode_mask=1,
+                       precessing=0),
+    # sixty days, five mode pairs, aligned, Keplerian orbits, TDI 2
+    "c2_hm_60d": dict(dt=5.0, n=1036800, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                      channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                      precessing=0),
+    # the same physics on shorter grids (sweep / parity sizes)
+    "c2_hm_7d": dict(dt=5.0, n=120960, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                     channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                     precessing=0),
+    "c2_hm_1d": dict(dt=5.0, n=17280, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                     channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                     precessing=0),
+    # precessing, five co-precessing modes, Keplerian, TDI 2
+    "c3_prec_60d": dict(dt=5.0, n=1036800, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                        channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                        precessing=1),
+    "c3_prec_1d": dict(dt=5.0, n=17280, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                       channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                       precessing=1),
+}
+
+DURATIONS_DAYS = (1, 7, 30, 60)                  # sweep: n = 17280, 120960, 518400, 1036800
+
+
+def config(name, **override):
+    c = dict(CONFIGS[name])
+    c.update(override)
+    return c
+
+
+def _sky(rng, w):
+    beta = np.arcsin(rng.uniform(-1.0, 1.0, w))
+    lam = rng.uniform(0.0, 2.0 * math.pi, w)
+    psi = rng.uniform(0.0, math.pi, w)
+    iota = np.arccos(rng.uniform(-1.0, 1.0, w))
+    phi = rng.uniform(0.0, 2.0 * math.pi, w)
+    return beta, lam, psi, iota, phi
+
+
+def c1_point(seed=1):
+    """The single source of the one-day workload: M = 1e6 Msun, q = 2,
+    chi1 = 0.5, chi2 = 0.3, merger parameter t_c = 0.75 d, sky / orientation
+    drawn from ``seed``.  D = 20 Gpc (rescaled by callers to a target SNR)."""
+    rng = np.random.default_rng(seed)
+    beta, lam, psi, iota, phi = _sky(rng, 1)
+    m1, m2 = 2.0e6 / 3.0, 1.0e6 / 3.0
+    return np.array([m1, m2, 0.5, 0.0, 0.0, 0.3, 0.0, 0.0, 20.0, iota[0], phi[0],
+                     beta[0], lam[0], psi[0], 0.75 * DAY])
+
+
+def prior_draws(w, n, dt, seed, precessing=False, tc_frac=(0.90, 0.98),
+                logm=(5.0, 7.0), q=(1.0, 8.0), logd=(0.0, 2.0)):
+    """Walkers drawn from the broad priors of the throughput workloads:
+    log-uniform total mass, uniform q, uniform aligned spins in [-0.99, 0.99]
+    (precessing: magnitudes in [0, 0.99], isotropic tilts), isotropic sky and
+    orientation, t_c uniform in a fraction of the window, D log-uniform [Gpc]."""
+    rng = np.random.default_rng(seed)
+    mt = 10.0 ** rng.uniform(logm[0], logm[1], w)
+    qq = rng.uniform(q[0], q[1], w)
+    m1 = mt * qq / (1.0 + qq)
+    m2 = mt / (1.0 + qq)
+    out = np.zeros((w, 15))
+    out[:, 0], out[:, 1] = m1, m2
+    if precessing:
+        out[:, 2] = rng.uniform(0.0, 0.99, w)
+        out[:, 3] = np.arccos(rng.uniform(-1.0, 1.0, w))
+        out[:, 4] = rng.uniform(0.0, 2.0 * math.pi, w)
+        out[:, 5] = rng.uniform(0.0, 0.99, w)
+        out[:, 6] = np.arccos(rng.uniform(-1.0, 1.0, w))
+        out[:, 7] = rng.uniform(0.0, 2.0 * math.pi, w)
+    else:
+        out[:, 2] = rng.uniform(-0.99, 0.99, w)
+        out[:, 5] = rng.uniform(-0.99, 0.99, w)
+    out[:, 8] = 10.0 ** rng.uniform(logd[0], logd[1], w)
+    beta, lam, psi, iota, phi = _sky(rng, w)
+    out[:, 9], out[:, 10], out[:, 11], out[:, 12], out[:, 13] = iota, phi, beta, lam, psi
+    out[:, 14] = rng.uniform(tc_frac[0], tc_frac[1], w) * n * dt
+    return out
+
+
+def table1_precessing(n, dt, tc_frac=0.9):
+    """The injection of Table I (precessing columns), t_c at a fraction of the window."""
+    r = math.radians
+    return np.array([1.0e6, 0.7e6, 0.7, r(40.1), r(40.1), 0.4, r(22.9), r(22.9), 20.0,
+                     r(149.0), r(229.2), r(-34.4), r(34.4), r(22.9), tc_frac * n * dt])
+
+
+def standard_normals(w, dim, seed):
+    """Standard normal draws (used as z in theta + L z perturbations)."""
+    return np.random.default_rng(seed).normal(size=(w, dim))
