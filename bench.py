@@ -1,0 +1,355 @@
+"""Benchmark: batched time-domain LISA log-likelihood evaluations per second.
+
+Workload (the headline configuration): 60 days at dt = 5 s (n = 1,036,800),
+256 walkers drawn from broad priors, modes (2,+-2),(2,+-1),(3,+-3),(3,+-2),
+(4,+-4), aligned spins, Keplerian unequal-arm orbits, TDI 2.0 -> A,E,T,
+Lagrange order 31, band [1e-4, 0.02] Hz, zero-noise injection data.
+One step = one lisa_td_loglike_batch over all walkers (waveform, projection,
+TDI, FFT, weighted norm).  `value` is the mixed-precision path; the FP64 GPU
+path is measured on the same inputs and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank drives one GPU with its own 256 walkers (weak scaling).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_hm_60d"
+WALKERS = 256
+METRIC = "logL evals/s (60 d @5 s, 256 walkers): mixed vs FP64 path at |dlogL|<=0.05"
+# nominal algorithmic FLOPs per walker-sample (FMA = 2; see the design notes)
+K_TAPS = 32
+FLOPS_PROJECT = 9 * (2 * 2 * K_TAPS + 4 * K_TAPS) + 6 * 32 + 9 * 5        # 2541
+FLOPS_TDI2 = 42 * 2 * K_TAPS + 6 + 10                                     # 2704
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5, max clock
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def _setup_gpu(local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2501_08261_gb300 import build
+    build.build()
+    from paper_2501_08261_gb300 import api, workloads
+    return torch, api, workloads
+
+
+def _gpu_kwargs(cfg):
+    return dict(dt=cfg["dt"], n=cfg["n"], t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
+                tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
+                lagrange_order=cfg["lagrange_order"], orbit=cfg["orbit"],
+                mode_mask=cfg["mode_mask"], precessing=cfg["precessing"])
+
+
+def _time_steps(torch, fn, steps, barrier):
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1)
+
+
+def cpu_baseline(cfg, theta, data_np, seconds_budget=20.0):
+    """The FP64 oracle on a bounded sample: one walker on a segment of the
+    workload's grid (same physics), scaled by n to full-length evals/s."""
+    import numpy as np
+    from oracle import pipeline
+    seg = min(cfg["n"], 129600)                       # 7.5 days
+    s = pipeline.Setup(dt=cfg["dt"], n=seg, t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
+                       tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
+                       lagrange_order=cfg["lagrange_order"],
+                       orbit={0: "rigid", 1: "kepler"}[cfg["orbit"]],
+                       mode_mask=cfg["mode_mask"], precessing=bool(cfg["precessing"]))
+    th = theta.copy()
+    th[14] = 0.9 * seg * cfg["dt"]
+    d = np.asarray(data_np)[:, :seg]
+    t = time.perf_counter()
+    reps = 0
+    while True:
+        pipeline.loglike(th, s, d)
+        reps += 1
+        if time.perf_counter() - t > seconds_budget * 0.5 or reps >= 3:
+            break
+    el = (time.perf_counter() - t) / reps
+    per_eval_full = el * cfg["n"] / seg
+    return {"value": 1.0 / per_eval_full, "unit": "logL evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 walker, {seg}-sample ({seg * cfg['dt'] / 86400:.1f} d) segment of the "
+                      f"workload, {reps} evals, {el:.2f} s each, scaled by n to the "
+                      f"{cfg['n']}-sample series"}
+
+
+def _inject(torch, api, lk_ref, lk_all, params, n, snr=2000.0):
+    """Zero-noise data: the response of walker 0 scaled to the given SNR; the
+    walker's distance is rescaled to match and walkers 1..7 sit near it."""
+    aet = lk_ref.tdi(lk_ref.project(params[:1])).reshape(3, n).contiguous()
+    lk_ref.set_data(aet)
+    far = params[:1].clone()
+    far[0, 8] = 1e30                                   # h -> 0: logL = -(d|d)/2
+    rho = math.sqrt(-2.0 * float(lk_ref.loglike(far)[0]))
+    aet = (aet * (snr / rho)).contiguous()
+    params[0, 8] *= rho / snr
+    params[1:8] = params[0]
+    params[1:8, 14] += torch.linspace(-0.1, 0.1, 7, dtype=params.dtype, device=params.device)
+    for lk in lk_all:
+        lk.set_data(aet)
+    return aet, rho
+
+
+def run_ours(args):
+    ws, rank, lrank = _dist()
+    torch, api, workloads = _setup_gpu(lrank)
+    import numpy as np
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lrank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cfg = workloads.config(args.workload)
+    kw = _gpu_kwargs(cfg)
+    W = args.walkers
+    theta = workloads.prior_draws(W, cfg["n"], cfg["dt"], seed=1000 + rank)
+    dev = torch.device("cuda", lrank)
+    params = torch.as_tensor(theta, device=dev)
+    lk32 = api.Likelihood(precision=1, max_walkers=W, **kw)
+    lk64 = None if args.skip_fp64 else api.Likelihood(precision=0, max_walkers=W, **kw)
+    aet, rho0 = _inject(torch, api, lk64 or lk32, [lk for lk in (lk32, lk64) if lk], params,
+                        cfg["n"])
+    theta = params.cpu().numpy()
+    logl = torch.empty(W, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step32():
+        api.lisa_td_loglike_batch(lk32.ctx, params, W, logl, None, stream)
+
+    def step64():
+        api.lisa_td_loglike_batch(lk64.ctx, params, W, logl, None, stream)
+
+    for _ in range(args.warmup):
+        step32()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(lrank)
+    clocks.start()
+    api.lisa_td_profile(lk32.ctx, 1)
+    ms32 = _time_steps(torch, step32, args.steps, barrier)
+    stages, ncalls = api.lisa_td_profile_read(lk32.ctx)
+    api.lisa_td_profile(lk32.ctx, 0)
+    clk = clocks.stop()
+    l32 = logl.clone()
+    # FP64 path: same inputs, fewer steps (it runs ~50x slower on this part)
+    k64 = max(1, min(args.steps, 2))
+    ms64, l64 = float("nan"), None
+    if lk64 is not None:
+        step64()
+        torch.cuda.synchronize()
+        ms64 = _time_steps(torch, step64, k64, barrier)
+        l64 = logl.clone()
+    # end to end through the public call: pinned host params in, logL out, per step
+    host_params = torch.as_tensor(theta).pin_memory()
+    host_logl = torch.empty(W, dtype=torch.float64).pin_memory()
+    dparams = torch.empty_like(params)
+
+    def step_e2e():
+        dparams.copy_(host_params, non_blocking=True)
+        api.lisa_td_loglike_batch(lk32.ctx, dparams, W, logl, None, stream)
+        host_logl.copy_(logl, non_blocking=True)
+
+    ms_e2e = float("nan")
+    if not args.skip_e2e:
+        step_e2e()
+        torch.cuda.synchronize()
+        ms_e2e = _time_steps(torch, step_e2e, args.steps, barrier)
+    # max over ranks
+    t32 = torch.tensor([ms32, ms64, ms_e2e], device=dev)
+    if dist is not None:
+        dist.all_reduce(t32, op=dist.ReduceOp.MAX)
+    ms32, ms64, ms_e2e = (float(x) for x in t32.tolist())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    evals = W * ws
+    value = evals * args.steps / (ms32 * 1e-3)
+    cmp = None
+    if l64 is not None:
+        d = (l32 - l64).abs().cpu().numpy()
+        a64 = l64.abs().cpu().numpy()
+        bulk = a64 <= 100.0
+        far = ~bulk
+        cmp = {"max_abs_dlogL_bulk": float(d[bulk].max()) if bulk.any() else None,
+               "bulk_walkers": int(bulk.sum()),
+               "max_rel_dlogL_far": float((d[far] / a64[far]).max()) if far.any() else None,
+               "snr_injection": 2000.0}
+    # roofline of the dominant stage (alu bound, FP32)
+    per_call = {k: v / max(ncalls, 1) for k, v in stages.items()}
+    dom = max(per_call, key=per_call.get)
+    flops_unit = {"project": FLOPS_PROJECT, "tdi": FLOPS_TDI2}.get(dom)
+    roof = None
+    if flops_unit is not None:
+        walker_samples = W * cfg["n"]
+        ach = flops_unit * walker_samples / (per_call[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
+                "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
+                "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal)"}
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "logL evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df32",
+        "data": "synthetic (seeded prior draws; zero-noise injection)",
+        "config": {"workload": "60 d @ 5 s (n=1036800), 256 walkers/GPU, HM (5 mode pairs), "
+                               "aligned, Keplerian unequal arms, TDI 2.0 AET, Lagrange p=31, "
+                               "band 1e-4..0.02 Hz",
+                   "walkers_per_gpu": W, "n": cfg["n"],
+                   "l2": "working set ~13 GB/step >> 129 MB L2 (no flush needed)"},
+        "fp64_path": {"value": round(evals * k64 / (ms64 * 1e-3), 3), "unit": "logL evals/s",
+                      "ms_per_step": round(ms64 / k64, 2), "steps": k64},
+        "mixed_vs_fp64": cmp,
+        "stage_ms": {k: round(v, 4) for k, v in per_call.items()},
+        "gpu_launches": 7 * args.steps,
+        "roofline": roof,
+        "clocks": clk,
+        "e2e": {"value": round(evals * args.steps / (ms_e2e * 1e-3), 2), "unit": "logL evals/s",
+                "h2d_bytes_per_step": W * 15 * 8, "d2h_bytes_per_step": W * 8},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, theta[0], aet.cpu().numpy())
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, each step a bounded sample."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+    from oracle import pipeline
+    from paper_2501_08261_gb300 import workloads
+    cfg = workloads.config(WORKLOAD)
+    seg = 34560                                        # 2-day segment per step
+    s = pipeline.Setup(dt=cfg["dt"], n=seg, f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
+                       tdi_gen=cfg["tdi_gen"], lagrange_order=cfg["lagrange_order"],
+                       orbit="kepler", mode_mask=cfg["mode_mask"])
+    theta = workloads.prior_draws(1, seg, cfg["dt"], seed=1000)[0]
+    d = pipeline.aet(theta, s)
+    for _ in range(args.warmup):
+        pipeline.loglike(theta, s, d)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        pipeline.loglike(theta, s, d)
+    el = time.perf_counter() - t
+    per_eval_full = el / args.steps * cfg["n"] / seg
+    v = 1.0 / per_eval_full
+    sample = (f"1 walker per step, {seg}-sample (2 d) segment of the workload, scaled by n "
+              f"to the {cfg['n']}-sample series")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "logL evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(el / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "60 d @ 5 s, HM, Keplerian, TDI 2.0 (oracle on 2-d segments)"},
+        "cpu_baseline": {"value": v, "unit": "logL evals/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "logL evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--walkers", type=int, default=WALKERS)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

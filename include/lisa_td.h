@@ -1,0 +1,123 @@
+/*
+ * lisa_td.h -- C ABI of the GB300 batched time-domain LISA log-likelihood.
+ *
+ * The library evaluates, for a batch of W walkers (parameter vectors), the
+ * full time-domain LISA likelihood of arXiv:2501.08261 (Sec. II):
+ *   waveform modes (Sec. II.A) -> polarisations h+, hx -> link responses y_slr
+ *   (Sec. II.B, Eq. yslr) -> TDI X, Y, Z (Sec. II.B, X_1.5 / X_2 equations and
+ *   cyclic permutation) -> A, E, T -> DFT -> PSD-weighted residual norm
+ *   logL = -1/2 sum_c (h_c - d_c | h_c - d_c) (Sec. II.B, inner product and
+ *   footnote on the complete log-likelihood).
+ *
+ * Conventions shared by every entry point
+ *   - All functions are extern "C", return int status: LISA_TD_OK (0) or a
+ *     negative LISA_TD_E* code; lisa_td_last_error() then describes the
+ *     failure (thread-local string, valid until the next call on the thread).
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *     The caller owns every input and output buffer; the library owns only the
+ *     context and the workspace it allocates in lisa_td_create().
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls only enqueue work on it and return; no host
+ *     synchronisation happens except in lisa_td_create / lisa_td_set_data
+ *     (which wait for their own set-up kernels).
+ *   - Parameter vectors: params_dev is FP64 [W][15], row-major, in the order
+ *       m1, m2 [Msun], a1 (chi1z if aligned), theta1, phi1, a2 (chi2z), theta2,
+ *       phi2, D [Gpc], iota, phi_ref, beta (ecliptic latitude), lambda
+ *       (ecliptic longitude), psi, t_c [s]   (angles in radians).
+ *     Table I of the paper lists the first fourteen; t_c is the time
+ *     parameter of the inspiral closed form.
+ *   - Sample index i <-> time t_i = t0 + i*dt, 0 <= i < n.
+ *   - Element type of h / y / aet buffers: double when precision == 0 (FP64
+ *     path), float when precision == 1 (mixed path: FP64 only for per-block
+ *     phase/time anchors, FP32 elsewhere).
+ */
+#ifndef LISA_TD_H
+#define LISA_TD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LISA_TD_OK        0
+#define LISA_TD_EINVAL   -1   /* bad argument (NULL pointer, size, option)       */
+#define LISA_TD_ENOMEM   -2   /* device allocation failed                        */
+#define LISA_TD_ECUDA    -3   /* a CUDA runtime call or kernel launch failed     */
+#define LISA_TD_ETIMEOUT -4   /* a bounded device-side wait gave up              */
+#define LISA_TD_ERANGE   -5   /* W above the context's max_walkers, n too large  */
+
+typedef struct lisa_td_ctx lisa_td_ctx;   /* opaque */
+
+typedef struct {
+  double  dt;              /* sample spacing [s] (Sec. II.C: 5 s)                 */
+  int64_t n;               /* samples per series, 2^a 3^b 5^c 7^d, 64..2^24       */
+  double  t0;              /* time of sample 0 [s]                               */
+  double  f_lo, f_hi;      /* inner-product band [Hz] (Sec. II.C)                */
+  int32_t tdi_gen;         /* 15 (X_1.5) or 20 (X_2)                             */
+  int32_t channel_mask;    /* bit0 A, bit1 E, bit2 T (Sec. III.D: A, AE, AET)   */
+  int32_t lagrange_order;  /* odd p in {1, 3, 5, ..., 31}; 1 = linear (Sec. II.B) */
+  int32_t orbit_kind;      /* 0 rigid equal-arm, 1 Keplerian unequal-arm         */
+  int32_t mode_mask;       /* bits (2,2),(2,1),(3,3),(3,2),(4,4) (Sec. II.A)     */
+  int32_t precessing;      /* 0 aligned spins, 1 precessing twist-up             */
+  int32_t precision;       /* 0 FP64, 1 mixed                                    */
+  int32_t max_walkers;     /* workspace is sized for this many walkers (>= 1)    */
+} lisa_td_config;
+
+/* Create a context: validates cfg, builds the orbit tables (one kernel, FP64),
+ * the PSD weights of the band bins and the FFT plan, and allocates the
+ * workspace for cfg->max_walkers walkers.  Sec. II.B: orbits "only need to be
+ * computed once".  On error *out is set to NULL. */
+int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream);
+
+/* Store the data d (A, E, T time series; FP64 device [3][n], row c = A,E,T).
+ * Sec. II.C: zero-noise injections, so d is normally an injected template.
+ * The library keeps its own copy; the call synchronises `stream`. */
+int lisa_td_set_data(lisa_td_ctx* ctx, const double* aet_dev, void* stream);
+
+/* Polarisations h+, hx (after the polarisation-angle rotation, Sec. III.A) on
+ * the grid for W walkers.  h_dev: [W][n][2] (h+, hx interleaved), element type
+ * per cfg.precision.  Sec. II.A (aligned modes; precessing: Eq. newtwistup). */
+int lisa_td_waveform(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
+                     void* h_dev, void* stream);
+
+/* Link responses y_slr (Eq. yslr) on the grid.  y_dev: [6][n][W] (link-major,
+ * then sample, walker fastest), link order l = 1, 2, 3, -1, -2, -3 where link
+ * l joins the two spacecraft other than |l| and (s, r) = (3,2), (1,3), (2,1),
+ * (2,3), (3,1), (1,2). */
+int lisa_td_project(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
+                    void* y_dev, void* stream);
+
+/* TDI X, Y, Z of generation cfg.tdi_gen from y (layout of lisa_td_project),
+ * then A, E, T (Sec. II.B).  aet_dev: [3][n][W], element type per precision. */
+int lisa_td_tdi(lisa_td_ctx* ctx, const void* y_dev, int32_t W, void* aet_dev,
+                void* stream);
+
+/* The hot path: logL[w] = -1/2 sum_{c in mask} (h_c - d_c | h_c - d_c) for
+ * W walkers.  logl_dev: FP64 [W].  status_dev: int32 [W] or NULL; a walker
+ * with non-finite or non-physical parameters gets status 1 and logL = -inf
+ * without failing the call.  Requires lisa_td_set_data first. */
+int lisa_td_loglike_batch(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
+                          double* logl_dev, int32_t* status_dev, void* stream);
+
+/* Stage timing of lisa_td_loglike_batch (measurement support, no paper
+ * counterpart).  lisa_td_profile(ctx, 1) makes the following loglike calls
+ * record a CUDA event on their stream before each stage and after the last
+ * (at most LISA_TD_PROF_CALLS calls are recorded; later calls run untimed).
+ * lisa_td_profile_read waits for the recorded events, writes the summed
+ * milliseconds of each stage to stage_ms[LISA_TD_NSTAGE] and the number of
+ * timed calls to *calls, and clears the record.  Stages: 0 prep, 1 waveform,
+ * 2 link projection, 3 TDI + A,E,T residual, 4 FFT pass 1, 5 FFT pass 2 +
+ * weighted norm, 6 final reduction. */
+#define LISA_TD_NSTAGE 7
+#define LISA_TD_PROF_CALLS 256
+int lisa_td_profile(lisa_td_ctx* ctx, int32_t enable);
+int lisa_td_profile_read(lisa_td_ctx* ctx, double* stage_ms, int64_t* calls);
+
+void lisa_td_destroy(lisa_td_ctx* ctx);
+const char* lisa_td_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LISA_TD_H */

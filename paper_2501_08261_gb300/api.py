@@ -1,0 +1,191 @@
+"""Thin ctypes binding of include/lisa_td.h (argument marshalling only).
+
+Every function has the C entry point's name and forwards device pointers
+(``tensor.data_ptr()``) and the CUDA stream handle; all arithmetic runs in the
+CUDA library.  If the library is missing, importing this module raises: there
+is no CPU fallback.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+LISA_TD_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
+EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
+           "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
+           "lisa_td_destroy", "lisa_td_last_error")
+NSTAGE = 7
+STAGES = ("prep", "waveform", "project", "tdi", "fft_pass1", "fft_pass2_norm", "reduce")
+
+
+class Config(ctypes.Structure):
+    """Mirror of lisa_td_config."""
+    _fields_ = [("dt", ctypes.c_double), ("n", ctypes.c_int64), ("t0", ctypes.c_double),
+                ("f_lo", ctypes.c_double), ("f_hi", ctypes.c_double),
+                ("tdi_gen", ctypes.c_int32), ("channel_mask", ctypes.c_int32),
+                ("lagrange_order", ctypes.c_int32), ("orbit_kind", ctypes.c_int32),
+                ("mode_mask", ctypes.c_int32), ("precessing", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_walkers", ctypes.c_int32)]
+
+
+def load_library(path=None):
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing: run paper_2501_08261_gb300.build "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    sig = {
+        "lisa_td_create": ([ctypes.POINTER(P), ctypes.POINTER(Config), P], ctypes.c_int),
+        "lisa_td_set_data": ([P, P, P], ctypes.c_int),
+        "lisa_td_waveform": ([P, P, I32, P, P], ctypes.c_int),
+        "lisa_td_project": ([P, P, I32, P, P], ctypes.c_int),
+        "lisa_td_tdi": ([P, P, I32, P, P], ctypes.c_int),
+        "lisa_td_loglike_batch": ([P, P, I32, P, P, P], ctypes.c_int),
+        "lisa_td_profile": ([P, I32], ctypes.c_int),
+        "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
+                                 ctypes.c_int),
+        "lisa_td_destroy": ([P], None),
+        "lisa_td_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_LIB = None
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+class LisaTdError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != LISA_TD_OK:
+        msg = lib().lisa_td_last_error().decode(errors="replace")
+        raise LisaTdError(f"{what} -> {ERRORS.get(rc, rc)}: {msg}")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def make_config(dt, n, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=15, channel_mask=7,
+                lagrange_order=31, orbit=0, mode_mask=1, precessing=0, precision=0,
+                max_walkers=32):
+    return Config(float(dt), int(n), float(t0), float(f_lo), float(f_hi), int(tdi_gen),
+                  int(channel_mask), int(lagrange_order), int(orbit), int(mode_mask),
+                  int(precessing), int(precision), int(max_walkers))
+
+
+def lisa_td_create(cfg, stream=None):
+    h = ctypes.c_void_p()
+    _check(lib().lisa_td_create(ctypes.byref(h), ctypes.byref(cfg), _stream(stream)),
+           "lisa_td_create")
+    return h
+
+
+def lisa_td_set_data(ctx, aet, stream=None):
+    _check(lib().lisa_td_set_data(ctx, _ptr(aet), _stream(stream)), "lisa_td_set_data")
+
+
+def lisa_td_waveform(ctx, params, W, h, stream=None):
+    _check(lib().lisa_td_waveform(ctx, _ptr(params), int(W), _ptr(h), _stream(stream)),
+           "lisa_td_waveform")
+
+
+def lisa_td_project(ctx, params, W, y, stream=None):
+    _check(lib().lisa_td_project(ctx, _ptr(params), int(W), _ptr(y), _stream(stream)),
+           "lisa_td_project")
+
+
+def lisa_td_tdi(ctx, y, W, aet, stream=None):
+    _check(lib().lisa_td_tdi(ctx, _ptr(y), int(W), _ptr(aet), _stream(stream)), "lisa_td_tdi")
+
+
+def lisa_td_loglike_batch(ctx, params, W, logl, status=None, stream=None):
+    _check(lib().lisa_td_loglike_batch(ctx, _ptr(params), int(W), _ptr(logl), _ptr(status),
+                                       _stream(stream)), "lisa_td_loglike_batch")
+
+
+def lisa_td_profile(ctx, enable):
+    _check(lib().lisa_td_profile(ctx, int(enable)), "lisa_td_profile")
+
+
+def lisa_td_profile_read(ctx):
+    """-> (dict stage -> summed ms, number of timed calls)"""
+    arr = (ctypes.c_double * NSTAGE)()
+    calls = ctypes.c_int64()
+    _check(lib().lisa_td_profile_read(ctx, arr, ctypes.byref(calls)), "lisa_td_profile_read")
+    return dict(zip(STAGES, list(arr))), calls.value
+
+
+def lisa_td_destroy(ctx):
+    lib().lisa_td_destroy(ctx)
+
+
+class Likelihood:
+    """Owns one context; tensors in, tensors out (torch on cuda)."""
+
+    def __init__(self, precision=0, max_walkers=32, stream=None, **cfg):
+        import torch
+        self.torch = torch
+        self.cfg = make_config(precision=precision, max_walkers=max_walkers, **cfg)
+        self.ctx = lisa_td_create(self.cfg, stream)
+        self.dtype = torch.float64 if precision == 0 else torch.float32
+
+    def close(self):
+        if self.ctx is not None:
+            lisa_td_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_data(self, aet):
+        lisa_td_set_data(self.ctx, aet.contiguous())
+
+    def waveform(self, params):
+        W = params.shape[0]
+        h = self.torch.empty((W, self.cfg.n, 2), dtype=self.dtype, device=params.device)
+        lisa_td_waveform(self.ctx, params.contiguous(), W, h)
+        return h
+
+    def project(self, params):
+        W = params.shape[0]
+        y = self.torch.empty((6, self.cfg.n, W), dtype=self.dtype, device=params.device)
+        lisa_td_project(self.ctx, params.contiguous(), W, y)
+        return y
+
+    def tdi(self, y):
+        W = y.shape[2]
+        aet = self.torch.empty((3, self.cfg.n, W), dtype=self.dtype, device=y.device)
+        lisa_td_tdi(self.ctx, y.contiguous(), W, aet)
+        return aet
+
+    def loglike(self, params, with_status=False):
+        W = params.shape[0]
+        out = self.torch.empty(W, dtype=self.torch.float64, device=params.device)
+        st = self.torch.empty(W, dtype=self.torch.int32, device=params.device)
+        lisa_td_loglike_batch(self.ctx, params.contiguous(), W, out, st)
+        return (out, st) if with_status else out

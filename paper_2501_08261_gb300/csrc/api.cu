@@ -1,0 +1,261 @@
+// C-ABI entry points of include/lisa_td.h: argument checks, context and
+// workspace ownership, and the launch sequence of each call.  No compute
+// happens on the host; every step of the likelihood runs in the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(LISA_TD_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(LISA_TD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(expr, where)                          \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+void free_ctx(lisa_td_ctx* c) {
+  if (!c) return;
+  if (c->prof_ev) {
+    for (int q = 0; q < LISA_TD_PROF_CALLS * (LISA_TD_NSTAGE + 1); ++q)
+      if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);
+    free(c->prof_ev);
+  }
+  void* ptrs[] = {c->orb64, c->orb32, c->psdw, c->plan.tw_n, c->plan.tw1, c->plan.tw2,
+                  c->tdi_tab, c->chan_list, c->data64, c->data32, c->walkers, c->h, c->y,
+                  c->r, c->fy, c->partial, c->status};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  free(c);
+}
+
+int check_cfg(const lisa_td_config* g) {
+  if (!(g->dt > 0.0) || !isfinite(g->dt)) return fail(LISA_TD_EINVAL, "dt must be > 0");
+  if (g->n < 64 || g->n > (int64_t(1) << 24)) return fail(LISA_TD_ERANGE, "n out of [64, 2^24]");
+  if (!isfinite(g->t0)) return fail(LISA_TD_EINVAL, "t0 must be finite");
+  if (!(g->f_lo >= 0.0) || !(g->f_hi > g->f_lo)) return fail(LISA_TD_EINVAL, "band must satisfy 0 <= f_lo < f_hi");
+  if (g->tdi_gen != 15 && g->tdi_gen != 20) return fail(LISA_TD_EINVAL, "tdi_gen must be 15 or 20");
+  if (g->channel_mask < 1 || g->channel_mask > 7) return fail(LISA_TD_EINVAL, "channel_mask must be in 1..7");
+  int p = g->lagrange_order;
+  if (!(p == 1 || p == 3 || p == 5 || p == 7 || p == 15 || p == 31))
+    return fail(LISA_TD_EINVAL, "lagrange_order must be one of 1, 3, 5, 7, 15, 31");
+  if (g->orbit_kind != 0 && g->orbit_kind != 1) return fail(LISA_TD_EINVAL, "orbit_kind must be 0 or 1");
+  if (g->mode_mask < 1 || g->mode_mask > 31) return fail(LISA_TD_EINVAL, "mode_mask must be in 1..31");
+  if (g->precessing != 0 && g->precessing != 1) return fail(LISA_TD_EINVAL, "precessing must be 0 or 1");
+  if (g->precision != 0 && g->precision != 1) return fail(LISA_TD_EINVAL, "precision must be 0 or 1");
+  if (g->max_walkers < 1 || g->max_walkers > 65536) return fail(LISA_TD_ERANGE, "max_walkers out of [1, 65536]");
+  return LISA_TD_OK;
+}
+
+int check_w(const lisa_td_ctx* c, int W) {
+  if (W < 1) return fail(LISA_TD_EINVAL, "W must be >= 1");
+  if (W > c->cfg.max_walkers) return fail(LISA_TD_ERANGE, "W=%d above max_walkers=%d", W, c->cfg.max_walkers);
+  return LISA_TD_OK;
+}
+
+inline int pad32(int w) { return (w + 31) / 32 * 32; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lisa_td_last_error(void) { return g_err; }
+
+int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
+  g_err[0] = 0;
+  if (!out) return fail(LISA_TD_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(LISA_TD_EINVAL, "cfg is NULL");
+  int rc = check_cfg(cfg);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  lisa_td_ctx* c = (lisa_td_ctx*)calloc(1, sizeof(lisa_td_ctx));
+  if (!c) return fail(LISA_TD_ENOMEM, "host allocation failed");
+  c->cfg = *cfg;
+  c->n = cfg->n;
+  c->wmax_pad = pad32(cfg->max_walkers);
+  c->esize = cfg->precision == 0 ? 8 : 4;
+  if (lisa::plan_fft(c->n, &c->plan) != 0) {
+    free_ctx(c);
+    return fail(LISA_TD_EINVAL, "n must be 2^a 3^b 5^c 7^d");
+  }
+  const int64_t n = c->n;
+  const size_t W = (size_t)c->wmax_pad;
+  const size_t cs = 2 * (size_t)c->esize;          // complex element
+  struct { void** p; size_t bytes; } allocs[] = {
+      {(void**)&c->orb64, sizeof(lisa::OrbitRec64) * n},
+      {(void**)&c->orb32, sizeof(lisa::OrbitRec32) * n},
+      {(void**)&c->psdw, sizeof(double) * 2 * (n / 2 + 1)},
+      {(void**)&c->plan.tw_n, cs * n},
+      {(void**)&c->plan.tw1, cs * c->plan.n1},
+      {(void**)&c->plan.tw2, cs * c->plan.n2},
+      {(void**)&c->tdi_tab, sizeof(lisa::TdiTable)},
+      {(void**)&c->chan_list, sizeof(int) * 3},
+      {(void**)&c->data64, sizeof(double) * 3 * n},
+      {(void**)&c->data32, sizeof(float) * 3 * n},
+      {(void**)&c->walkers, sizeof(lisa::WalkerRec) * W},
+      {(void**)&c->h, cs * n * W},
+      {(void**)&c->y, (size_t)c->esize * 6 * n * W},
+      {(void**)&c->r, (size_t)c->esize * 3 * n * W},
+      {(void**)&c->fy, (size_t)c->esize * 3 * n * W},
+      {(void**)&c->partial, sizeof(double) * 3 * (c->plan.n1 / 2 + 1) * W},
+      {(void**)&c->status, sizeof(int32_t) * W},
+  };
+  for (auto& a : allocs) {
+    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    if (e != cudaSuccess) {
+      *a.p = nullptr;
+      free_ctx(c);
+      cudaGetLastError();
+      return cuda_fail(e, "lisa_td_create: cudaMalloc");
+    }
+  }
+  lisa::TdiTable tab = lisa::build_tdi_table(cfg->tdi_gen);
+  c->tdi_nd = tab.max_links_in_delay;
+  int chans[3] = {0, 0, 0}, nch = 0;
+  for (int q = 0; q < 3; ++q)
+    if ((cfg->channel_mask >> q) & 1) chans[nch++] = q;
+  cudaError_t e = cudaMemcpyAsync(c->tdi_tab, &tab, sizeof(tab), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->chan_list, chans, sizeof(chans), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->data64, 0, sizeof(double) * 3 * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->data32, 0, sizeof(float) * 3 * n, s);
+  if (e == cudaSuccess) e = lisa::launch_orbit_tables(c, s);
+  if (e == cudaSuccess) e = lisa::launch_psd_weights(c, s);
+  if (e == cudaSuccess) e = lisa::launch_twiddles(c, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_ctx(c);
+    return cuda_fail(e, "lisa_td_create");
+  }
+  *out = c;
+  return LISA_TD_OK;
+}
+
+int lisa_td_set_data(lisa_td_ctx* c, const double* aet_dev, void* stream) {
+  g_err[0] = 0;
+  if (!c || !aet_dev) return fail(LISA_TD_EINVAL, "NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(lisa::launch_data_copy(c, aet_dev, s), "lisa_td_set_data");
+  CK(cudaStreamSynchronize(s), "lisa_td_set_data");
+  c->has_data = 1;
+  return LISA_TD_OK;
+}
+
+int lisa_td_waveform(lisa_td_ctx* c, const double* params_dev, int32_t W, void* h_dev,
+                     void* stream) {
+  g_err[0] = 0;
+  if (!c || !params_dev || !h_dev) return fail(LISA_TD_EINVAL, "NULL argument");
+  int rc = check_w(c, W);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(lisa::launch_prep(c, params_dev, W, pad32(W), s), "lisa_td_waveform: prep");
+  CK(lisa::launch_waveform(c, W, h_dev, s), "lisa_td_waveform");
+  return LISA_TD_OK;
+}
+
+int lisa_td_project(lisa_td_ctx* c, const double* params_dev, int32_t W, void* y_dev,
+                    void* stream) {
+  g_err[0] = 0;
+  if (!c || !params_dev || !y_dev) return fail(LISA_TD_EINVAL, "NULL argument");
+  int rc = check_w(c, W);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int Wp = pad32(W);
+  CK(lisa::launch_prep(c, params_dev, W, Wp, s), "lisa_td_project: prep");
+  CK(lisa::launch_waveform(c, Wp, c->h, s), "lisa_td_project: waveform");
+  CK(lisa::launch_project(c, W, W, c->h, y_dev, s), "lisa_td_project");
+  return LISA_TD_OK;
+}
+
+int lisa_td_tdi(lisa_td_ctx* c, const void* y_dev, int32_t W, void* aet_dev, void* stream) {
+  g_err[0] = 0;
+  if (!c || !y_dev || !aet_dev) return fail(LISA_TD_EINVAL, "NULL argument");
+  int rc = check_w(c, W);
+  if (rc) return rc;
+  CK(lisa::launch_tdi(c, W, W, y_dev, aet_dev, 0, (cudaStream_t)stream), "lisa_td_tdi");
+  return LISA_TD_OK;
+}
+
+int lisa_td_loglike_batch(lisa_td_ctx* c, const double* params_dev, int32_t W, double* logl_dev,
+                          int32_t* status_dev, void* stream) {
+  g_err[0] = 0;
+  if (!c || !params_dev || !logl_dev) return fail(LISA_TD_EINVAL, "NULL argument");
+  int rc = check_w(c, W);
+  if (rc) return rc;
+  if (!c->has_data) return fail(LISA_TD_EINVAL, "lisa_td_set_data has not been called");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int Wp = pad32(W);
+  cudaEvent_t* ev = nullptr;
+  if (c->prof_on && c->prof_calls < LISA_TD_PROF_CALLS)
+    ev = c->prof_ev + (size_t)(c->prof_calls++) * (LISA_TD_NSTAGE + 1);
+#define STAGE(k, call, what)                                \
+  do {                                                      \
+    if (ev) CK(cudaEventRecord(ev[k], s), "loglike: event"); \
+    CK(call, what);                                         \
+  } while (0)
+  STAGE(0, lisa::launch_prep(c, params_dev, W, Wp, s), "loglike: prep");
+  STAGE(1, lisa::launch_waveform(c, Wp, c->h, s), "loglike: waveform");
+  STAGE(2, lisa::launch_project(c, Wp, Wp, c->h, c->y, s), "loglike: project");
+  STAGE(3, lisa::launch_tdi(c, Wp, Wp, c->y, c->r, 1, s), "loglike: tdi");
+  STAGE(4, lisa::launch_fft_pass1(c, Wp, c->r, s), "loglike: fft pass 1");
+  STAGE(5, lisa::launch_fft_pass2(c, Wp, s), "loglike: fft pass 2");
+  STAGE(6, lisa::launch_reduce(c, W, Wp, logl_dev, status_dev, s), "loglike: reduce");
+#undef STAGE
+  if (ev) CK(cudaEventRecord(ev[LISA_TD_NSTAGE], s), "loglike: event");
+  return LISA_TD_OK;
+}
+
+int lisa_td_profile(lisa_td_ctx* c, int32_t enable) {
+  g_err[0] = 0;
+  if (!c) return fail(LISA_TD_EINVAL, "NULL context");
+  if (enable && !c->prof_ev) {
+    const int m = LISA_TD_PROF_CALLS * (LISA_TD_NSTAGE + 1);
+    c->prof_ev = (cudaEvent_t*)calloc(m, sizeof(cudaEvent_t));
+    if (!c->prof_ev) return fail(LISA_TD_ENOMEM, "host allocation failed");
+    for (int q = 0; q < m; ++q) CK(cudaEventCreate(&c->prof_ev[q]), "lisa_td_profile");
+  }
+  c->prof_on = enable ? 1 : 0;
+  c->prof_calls = 0;
+  return LISA_TD_OK;
+}
+
+int lisa_td_profile_read(lisa_td_ctx* c, double* stage_ms, int64_t* calls) {
+  g_err[0] = 0;
+  if (!c || !stage_ms || !calls) return fail(LISA_TD_EINVAL, "NULL argument");
+  for (int k = 0; k < LISA_TD_NSTAGE; ++k) stage_ms[k] = 0.0;
+  *calls = c->prof_calls;
+  for (int q = 0; q < c->prof_calls; ++q) {
+    cudaEvent_t* ev = c->prof_ev + (size_t)q * (LISA_TD_NSTAGE + 1);
+    CK(cudaEventSynchronize(ev[LISA_TD_NSTAGE]), "lisa_td_profile_read");
+    for (int k = 0; k < LISA_TD_NSTAGE; ++k) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, ev[k], ev[k + 1]), "lisa_td_profile_read");
+      stage_ms[k] += ms;
+    }
+  }
+  c->prof_calls = 0;
+  return LISA_TD_OK;
+}
+
+void lisa_td_destroy(lisa_td_ctx* c) { free_ctx(c); }
+
+}  // extern "C"

@@ -1,0 +1,291 @@
+// DFT of the A, E, T residuals and the PSD-weighted norm (Sec. II.B):
+//   logL = -1/2 sum_c 4 df sum_{k in band} |dt DFT(h_c - d_c)_k|^2 / S_c(f_k).
+//
+// Four-step mixed-radix FFT, n = n1 * n2, input index i = n2 * a + b, output
+// bin k = k1 + n1 * k2.  Two real series (walkers 2p and 2p+1, adjacent in the
+// walker-minor layout) form one complex sequence z = x_2p + i x_2p+1.
+//   pass 1: for each b, an n1-point transform over a, times W_n^{b k1}
+//   pass 2: for each row pair (k1, n1 - k1), n2-point transforms over b; the
+//           two rows hold every bin together with its mirror n - k, so the two
+//           walkers separate as X = (Z_k + conj Z_{n-k})/2, Y = (Z_k - conj Z_{n-k})/2i,
+//           and the weighted |.|^2 of the band bins (k <= n/2) is summed.
+// The n1- and n2-point transforms are Stockham radix-2/3/4/5/7/8 stages in
+// shared memory, pairs of walkers along the fast axis.
+#include <math.h>
+
+#include "internal.h"
+
+namespace lisa {
+
+namespace {
+
+template <typename R> struct CT;
+template <> struct CT<double> { using T = double2; };
+template <> struct CT<float> { using T = float2; };
+
+template <typename C>
+__device__ inline C cmulv(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+
+struct Radices { int r[kMaxRadix]; int nr; };
+
+// one Stockham stage of radix RAD: A (natural sub-blocks of length L) -> B
+template <int RAD, typename C>
+__device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, int P,
+                      const C* __restrict__ tw, int tid, int nth) {
+  const int nb = m / RAD;
+  const int stride = m / (L * RAD);
+  const int rstep = m / RAD;
+  for (int item = tid; item < nb * P; item += nth) {
+    const int p = item % P, j = item / P;
+    const int k = j % L;
+    C a[RAD];
+#pragma unroll
+    for (int q = 0; q < RAD; ++q) {
+      a[q] = A[(j + q * nb) * P + p];
+      if (q > 0 && k > 0) a[q] = cmulv(a[q], tw[k * q * stride]);
+    }
+    const int base = (j - k) * RAD + k;
+#pragma unroll
+    for (int s = 0; s < RAD; ++s) {
+      C b = a[0];
+#pragma unroll
+      for (int q = 1; q < RAD; ++q) {
+        C t = cmulv(a[q], tw[((q * s) % RAD) * rstep]);
+        b.x += t.x;
+        b.y += t.y;
+      }
+      B[(base + s * L) * P + p] = b;
+    }
+  }
+}
+
+// full m-point transform of P columns; returns the buffer holding the result
+template <typename C>
+__device__ C* transform(C* buf0, C* buf1, int m, int P, const Radices& rd,
+                        const C* __restrict__ tw) {
+  C* A = buf0;
+  C* B = buf1;
+  int L = 1;
+  for (int s = 0; s < rd.nr; ++s) {
+    const int r = rd.r[s];
+    switch (r) {
+      case 2: stage<2>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      case 3: stage<3>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      case 4: stage<4>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      case 5: stage<5>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      case 7: stage<7>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      default: stage<8>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+    }
+    __syncthreads();
+    C* t = A;
+    A = B;
+    B = t;
+    L *= r;
+  }
+  return A;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) pass1_kernel(const R* __restrict__ x,
+                                                    typename CT<R>::T* __restrict__ fy, int64_t n,
+                                                    int n1, int n2, int Pt, int Pb, Radices rd,
+                                                    const typename CT<R>::T* __restrict__ tw1,
+                                                    const typename CT<R>::T* __restrict__ twn,
+                                                    const int* __restrict__ chans) {
+  using C = typename CT<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  C* b0 = reinterpret_cast<C*>(smem_raw);
+  C* b1 = b0 + (size_t)n1 * Pb;
+  const int b = blockIdx.x;
+  const int pb0 = blockIdx.y * Pb;
+  const int c = chans[blockIdx.z];
+  const int Wpad = 2 * Pt;
+  const C* xc = reinterpret_cast<const C*>(x + (int64_t)c * n * Wpad);
+  for (int item = threadIdx.x; item < n1 * Pb; item += blockDim.x) {
+    const int a = item / Pb, p = item % Pb;
+    b0[item] = xc[((int64_t)n2 * a + b) * Pt + pb0 + p];
+  }
+  __syncthreads();
+  C* res = transform(b0, b1, n1, Pb, rd, tw1);
+  C* out = fy + (int64_t)c * n * Pt;
+  for (int item = threadIdx.x; item < n1 * Pb; item += blockDim.x) {
+    const int k1 = item / Pb, p = item % Pb;
+    C v = cmulv(res[item], twn[(int64_t)b * k1]);
+    out[((int64_t)k1 * n2 + b) * Pt + pb0 + p] = v;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) pass2_kernel(const typename CT<R>::T* __restrict__ fy,
+                                                    double* __restrict__ partial, int64_t n,
+                                                    int n1, int n2, int Pt, int Pb, Radices rd,
+                                                    const typename CT<R>::T* __restrict__ tw2,
+                                                    const double* __restrict__ psdw,
+                                                    const int* __restrict__ chans) {
+  using C = typename CT<R>::T;
+  extern __shared__ unsigned char smem_raw[];
+  C* a0 = reinterpret_cast<C*>(smem_raw);
+  C* a1 = a0 + (size_t)n2 * Pb;
+  C* c0 = a1 + (size_t)n2 * Pb;
+  C* c1 = c0 + (size_t)n2 * Pb;
+  __shared__ double red[256];
+  const int rp = blockIdx.x;
+  const int pb0 = blockIdx.y * Pb;
+  const int c = chans[blockIdx.z];
+  const int rA = rp, rB = (n1 - rp) % n1;
+  const bool single = (rA == rB);
+  const C* in = fy + (int64_t)c * n * Pt;
+  for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
+    const int j = item / Pb, p = item % Pb;
+    a0[item] = in[((int64_t)rA * n2 + j) * Pt + pb0 + p];
+    if (!single) c0[item] = in[((int64_t)rB * n2 + j) * Pt + pb0 + p];
+  }
+  __syncthreads();
+  C* XA = transform(a0, a1, n2, Pb, rd, tw2);
+  C* XB = single ? XA : transform(c0, c1, n2, Pb, rd, tw2);
+  const int64_t nb = n / 2 + 1;
+  const double* wv = psdw + (c == 2 ? nb : 0);
+  double accx = 0.0, accy = 0.0;           // walker 2p, 2p+1 (p fixed per thread)
+  const int nrow = single ? 1 : 2;
+  for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
+    const int k2 = item / Pb, p = item % Pb;
+    for (int rr = 0; rr < nrow; ++rr) {
+      const C* X = rr == 0 ? XA : XB;
+      const C* Xm = rr == 0 ? XB : XA;
+      const int row = rr == 0 ? rA : rB;
+      const int64_t k = row + (int64_t)n1 * k2;
+      if (k >= nb) continue;
+      const double wk = wv[k];
+      if (wk == 0.0) continue;
+      const int km = (single && row == 0) ? (n2 - k2) % n2 : n2 - 1 - k2;
+      C z = X[k2 * Pb + p];
+      C zm = Xm[km * Pb + p];
+      double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
+      double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
+      accx += wk * (xr * xr + xi * xi);
+      accy += wk * (yr * yr + yi * yi);
+    }
+  }
+  // per-column reduction: thread t always served column t % Pb (blockDim % Pb == 0)
+  const int p = threadIdx.x % Pb;
+  for (int half = 0; half < 2; ++half) {
+    red[threadIdx.x] = half == 0 ? accx : accy;
+    __syncthreads();
+    if (threadIdx.x < Pb) {
+      double s = 0.0;
+      for (int t = threadIdx.x; t < (int)blockDim.x; t += Pb) s += red[t];
+      partial[((int64_t)c * (n1 / 2 + 1) + rp) * (2 * Pt) + 2 * (pb0 + p) + half] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void reduce_kernel(const double* __restrict__ partial, int nrp, int Wpad, int W,
+                              int mask, const WalkerRec* __restrict__ walkers, double* logl,
+                              int32_t* status) {
+  int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  double s = 0.0;
+  for (int c = 0; c < 3; ++c) {
+    if (!((mask >> c) & 1)) continue;
+    for (int r = 0; r < nrp; ++r) s += partial[((int64_t)c * nrp + r) * Wpad + w];
+  }
+  int st = walkers[w].status;
+  logl[w] = st ? -INFINITY : -0.5 * s;
+  if (status) status[w] = st;
+}
+
+int pick_pb(int m, int nbuf, size_t csize, int Pt) {
+  int pb = 16;
+  while (pb > 1 && ((size_t)nbuf * m * pb * csize > 200 * 1024 || Pt % pb != 0)) pb /= 2;
+  return ((size_t)nbuf * m * pb * csize > 200 * 1024) ? 0 : pb;
+}
+
+void radices_of(int m, Radices* rd) {
+  rd->nr = 0;
+  while (m % 8 == 0) { rd->r[rd->nr++] = 8; m /= 8; }
+  while (m % 4 == 0) { rd->r[rd->nr++] = 4; m /= 4; }
+  while (m % 2 == 0) { rd->r[rd->nr++] = 2; m /= 2; }
+  while (m % 3 == 0) { rd->r[rd->nr++] = 3; m /= 3; }
+  while (m % 5 == 0) { rd->r[rd->nr++] = 5; m /= 5; }
+  while (m % 7 == 0) { rd->r[rd->nr++] = 7; m /= 7; }
+}
+
+template <typename R>
+cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cudaStream_t s) {
+  using C = typename CT<R>::T;
+  const FftPlan& p = c->plan;
+  const int Pt = Wpad / 2;
+  int chans_h[3], nch = 0;
+  for (int q = 0; q < 3; ++q)
+    if ((c->cfg.channel_mask >> q) & 1) chans_h[nch++] = q;
+  Radices r1, r2;
+  r1.nr = p.nr1;
+  r2.nr = p.nr2;
+  for (int q = 0; q < p.nr1; ++q) r1.r[q] = p.r1[q];
+  for (int q = 0; q < p.nr2; ++q) r2.r[q] = p.r2[q];
+  int pb1 = pick_pb(p.n1, 2, sizeof(C), Pt);
+  int pb2 = pick_pb(p.n2, 4, sizeof(C), Pt);
+  if (pb1 == 0 || pb2 == 0) return cudaErrorInvalidValue;
+  size_t sm1 = (size_t)2 * p.n1 * pb1 * sizeof(C);
+  size_t sm2 = (size_t)4 * p.n2 * pb2 * sizeof(C);
+  cudaFuncSetAttribute(pass1_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+  cudaFuncSetAttribute(pass2_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+  const int* chans = c->chan_list;
+  if (pass == 1) {
+    dim3 g1((unsigned)p.n2, (unsigned)(Pt / pb1), (unsigned)nch);
+    pass1_kernel<R><<<g1, 256, sm1, s>>>((const R*)r, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
+                                         (const C*)p.tw1, (const C*)p.tw_n, chans);
+  } else {
+    dim3 g2((unsigned)(p.n1 / 2 + 1), (unsigned)(Pt / pb2), (unsigned)nch);
+    pass2_kernel<R><<<g2, 256, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
+                                         pb2, r2, (const C*)p.tw2, c->psdw, chans);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int plan_fft(int64_t n, FftPlan* p) {
+  int64_t m = n;
+  for (int f : {2, 3, 5, 7})
+    while (m % f == 0) m /= f;
+  if (m != 1 || n < 4) return -1;
+  int64_t best = 1;
+  for (int64_t d = 1; d * d <= n; ++d)
+    if (n % d == 0) best = d;
+  p->n1 = (int)best;
+  p->n2 = (int)(n / best);
+  Radices a, b;
+  radices_of(p->n1, &a);
+  radices_of(p->n2, &b);
+  p->nr1 = a.nr;
+  p->nr2 = b.nr;
+  for (int q = 0; q < a.nr; ++q) p->r1[q] = a.r[q];
+  for (int q = 0; q < b.nr; ++q) p->r2[q] = b.r[q];
+  return 0;
+}
+
+cudaError_t launch_fft_pass1(const lisa_td_ctx* c, int Wpad, const void* r, cudaStream_t s) {
+  return c->cfg.precision == 0 ? launch_t<double>(c, Wpad, r, 1, s)
+                               : launch_t<float>(c, Wpad, r, 1, s);
+}
+
+cudaError_t launch_fft_pass2(const lisa_td_ctx* c, int Wpad, cudaStream_t s) {
+  return c->cfg.precision == 0 ? launch_t<double>(c, Wpad, nullptr, 2, s)
+                               : launch_t<float>(c, Wpad, nullptr, 2, s);
+}
+
+cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl, int32_t* status,
+                          cudaStream_t s) {
+  reduce_kernel<<<(W + 127) / 128, 128, 0, s>>>(c->partial, c->plan.n1 / 2 + 1, Wpad, W,
+                                                c->cfg.channel_mask, c->walkers, logl, status);
+  return cudaGetLastError();
+}
+
+}  // namespace lisa

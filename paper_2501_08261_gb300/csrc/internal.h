@@ -1,0 +1,80 @@
+// Host-side internals: the context object and the kernel launchers that the
+// C-ABI entry points in api.cu sequence.  Not part of the public header.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/lisa_td.h"
+#include "common.cuh"
+
+namespace lisa {
+
+constexpr int kMaxRadix = 16;
+
+struct FftPlan {
+  int n1, n2;                      // n = n1 * n2 (n2 contiguous in pass 1's input)
+  int r1[kMaxRadix], nr1;          // radix sequence of the n1-point transforms
+  int r2[kMaxRadix], nr2;          // radix sequence of the n2-point transforms
+  void* tw_n;                      // W_n^j, j < n          (double2 / float2)
+  void* tw1;                       // W_n1^j, j < n1
+  void* tw2;                       // W_n2^j, j < n2
+};
+
+}  // namespace lisa
+
+struct lisa_td_ctx {
+  lisa_td_config cfg;
+  int64_t n;
+  int wmax_pad;                    // max walkers rounded up to 32
+  int esize;                       // 8 (FP64) or 4 (mixed)
+  lisa::OrbitRec64* orb64;
+  lisa::OrbitRec32* orb32;
+  double* psdw;                    // [2][n/2+1]: dt^2 * 4 df / S (AE, T) in band, else 0
+  lisa::FftPlan plan;
+  lisa::TdiTable* tdi_tab;         // device copy of the TDI term table
+  int tdi_nd;                      // most light times in one delay
+  int* chan_list;                  // device [3]: indices of the channels in the mask
+  double* data64;                  // [3][n]
+  float* data32;                   // [3][n]
+  int has_data;
+  // workspace
+  lisa::WalkerRec* walkers;        // [wmax_pad]
+  void* h;                         // [wmax_pad][n][2]
+  void* y;                         // [6][n][wmax_pad]
+  void* r;                         // [3][n][wmax_pad]
+  void* fy;                        // [3][n1][n2][wmax_pad/2] complex
+  double* partial;                 // [3][n1/2+1][wmax_pad]
+  int32_t* status;                 // [wmax_pad]
+  // stage timing (lisa_td_profile)
+  int prof_on;
+  int prof_calls;
+  cudaEvent_t* prof_ev;            // [LISA_TD_PROF_CALLS][LISA_TD_NSTAGE + 1]
+};
+
+namespace lisa {
+
+// prep.cu
+cudaError_t launch_prep(const lisa_td_ctx* c, const double* params, int W, int Wpad,
+                        cudaStream_t s);
+// orbit.cu (create-time tables)
+cudaError_t launch_orbit_tables(const lisa_td_ctx* c, cudaStream_t s);
+cudaError_t launch_psd_weights(const lisa_td_ctx* c, cudaStream_t s);
+cudaError_t launch_twiddles(const lisa_td_ctx* c, cudaStream_t s);
+cudaError_t launch_data_copy(const lisa_td_ctx* c, const double* aet, cudaStream_t s);
+// waveform.cu: h[w][i][2] for w < W (row stride n)
+cudaError_t launch_waveform(const lisa_td_ctx* c, int W, void* h, cudaStream_t s);
+// project.cu: y[l][i][ldw] for w < W, from the walker-major h with Wpad rows
+cudaError_t launch_project(const lisa_td_ctx* c, int W, int ldw, const void* h, void* y,
+                           cudaStream_t s);
+// tdi.cu: out[c][i][ldw] = AET (resid = 0) or AET - data (resid = 1)
+cudaError_t launch_tdi(const lisa_td_ctx* c, int W, int ldw, const void* y, void* out,
+                       int resid, cudaStream_t s);
+// fft.cu: residual r[3][n][Wpad] -> (pass 1) -> (pass 2 + weighted norm) partial sums
+cudaError_t launch_fft_pass1(const lisa_td_ctx* c, int Wpad, const void* r, cudaStream_t s);
+cudaError_t launch_fft_pass2(const lisa_td_ctx* c, int Wpad, cudaStream_t s);
+cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl,
+                          int32_t* status, cudaStream_t s);
+int plan_fft(int64_t n, FftPlan* p);
+TdiTable build_tdi_table(int gen);
+
+}  // namespace lisa

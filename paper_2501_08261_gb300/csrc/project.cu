@@ -1,0 +1,277 @@
+// Link responses y_slr on the grid (Sec. II.B, Eq. yslr):
+//   n = unit(r_r(t) - r_s(t - L_l)), x+ = (u.n)^2 - (v.n)^2, xx = (u.n)(v.n),
+//   t_s = t - L_l - k.r_s,  t_r = t - k.r_r,
+//   y = [x+ (h+(t_s) - h+(t_r)) + 2 xx (hx(t_s) - hx(t_r))] / (2 (1 - k.n)),
+// h at t_s, t_r by centred Lagrange interpolation (zero outside the grid).
+//
+// Layout: one CTA = 32 walkers (lanes) x a tile of samples (warps stride the
+// tile).  Each walker's h window, shifted by its own barycentric delay
+// k.g(t)/dt, is staged in shared memory [row][walker] (rows padded to 33) so
+// that the nine stencils of every sample read conflict-free columns.
+#include <math.h>
+
+#include "internal.h"
+#include "lagrange.cuh"
+
+namespace lisa {
+
+namespace {
+
+constexpr int kPW = 33;                 // padded walkers per shared-memory row
+
+template <int K>
+__global__ void __launch_bounds__(128) project_fp64_kernel(
+    const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
+    const OrbitRec64* __restrict__ orb, const double2* __restrict__ h, double* __restrict__ y,
+    int tile, int halo) {
+  extern __shared__ double2 win[];      // [(tile + 2 halo)][kPW]
+  __shared__ int shift_s[32];
+  __shared__ double cinv_s[K];
+  const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+  const int tid = warp * 32 + lane;
+  const int64_t i0 = (int64_t)blockIdx.x * tile;
+  const int w = blockIdx.y * 32 + lane;
+  const int rows = tile + 2 * halo;
+  if (tid < K) cinv_s[tid] = lagrange_denom_inv<double, K>(tid);
+  if (warp == 0) {
+    const WalkerRec& R = walkers[w];
+    double tc = t0 + ((double)i0 + 0.5 * tile) * dt;
+    double a = kOmegaOrb * tc;
+    double S = kAUSec * (R.k[0] * cos(a) + R.k[1] * sin(a));
+    shift_s[lane] = (int)floor(S / dt);
+  }
+  __syncthreads();
+  // stage: warp q loads walkers q, q + nw, ... (coalesced along samples)
+  for (int ww = warp; ww < 32; ww += nw) {
+    const int64_t a0 = i0 - shift_s[ww] - halo;
+    const double2* hw = h + (int64_t)(blockIdx.y * 32 + ww) * n;
+    for (int r = lane; r < rows; r += 32) {
+      int64_t g = a0 + r;
+      win[r * kPW + ww] = (g >= 0 && g < n) ? hw[g] : make_double2(0.0, 0.0);
+    }
+  }
+  __syncthreads();
+  const WalkerRec& R = walkers[w];
+  const double k0 = R.k[0], k1 = R.k[1], k2 = R.k[2];
+  const int64_t a0 = i0 - shift_s[lane] - halo;
+  const double2* hw = h + (int64_t)w * n;
+  double cinv[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
+
+  auto interp = [&](double tau, double& hp, double& hc) {
+    double fl = floor(tau);
+    double eps = tau - fl;
+    double wts[K];
+    lagrange_weights<double, K>(eps, cinv, wts);
+    int64_t base = (int64_t)fl - (K - 2) / 2;
+    int64_t loc = base - a0;
+    double sp = 0.0, sc = 0.0;
+    if (loc >= 0 && loc + K <= rows) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        double2 v = win[(loc + j) * kPW + lane];
+        sp += wts[j] * v.x;
+        sc += wts[j] * v.y;
+      }
+    } else {                                   // outside the staged window: global reads
+      for (int j = 0; j < K; ++j) {
+        int64_t g = base + j;
+        if (g >= 0 && g < n) {
+          double2 v = hw[g];
+          sp += wts[j] * v.x;
+          sc += wts[j] * v.y;
+        }
+      }
+    }
+    hp = sp;
+    hc = sc;
+  };
+
+  for (int s = warp; s < tile; s += nw) {
+    const int64_t i = i0 + s;
+    if (i >= n) break;
+    const OrbitRec64& O = orb[i];
+    double hpr[3], hcr[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double kr = k0 * O.rr[q][0] + k1 * O.rr[q][1] + k2 * O.rr[q][2];
+      interp((double)i - kr / dt, hpr[q], hcr[q]);
+    }
+#pragma unroll
+    for (int j = 0; j < kNLink; ++j) {
+      const int rq = link_receiver(j);
+      double ks = k0 * O.rs[j][0] + k1 * O.rs[j][1] + k2 * O.rs[j][2];
+      double hps, hcs;
+      interp((double)i - (O.L[j] + ks) / dt, hps, hcs);
+      double nx = O.n[j][0], ny = O.n[j][1], nz = O.n[j][2];
+      double un = R.u[0] * nx + R.u[1] * ny + R.u[2] * nz;
+      double vn = R.v[0] * nx + R.v[1] * ny + R.v[2] * nz;
+      double kn = k0 * nx + k1 * ny + k2 * nz;
+      double val = ((un * un - vn * vn) * (hps - hpr[rq]) + 2.0 * un * vn * (hcs - hcr[rq])) /
+                   (2.0 * (1.0 - kn));
+      if (w < W) y[((int64_t)j * n + i) * ldw + w] = val;
+    }
+  }
+}
+
+// Mixed path.  Per tile and walker one FP64 anchor S_a = k.g(t_a) (split into
+// an integer sample shift and a fraction); per sample the change of k.g over
+// the tile (a second-order expansion in Omega dt, error < 1e-9 s) and the
+// spacecraft offsets k.rho (FP32 table relative to g) enter only as small
+// FP32 numbers next to exact integers.
+template <int K>
+__global__ void __launch_bounds__(128) project_mixed_kernel(
+    const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
+    const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
+    int tile, int halo, int nL, float rL) {
+  extern __shared__ float2 winf[];      // [(tile + 2 halo)][kPW]
+  __shared__ int shift_s[32];
+  __shared__ float fra_s[32], p1_s[32], sa_s[32];
+  __shared__ float cinv_s[K];
+  const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
+  const int tid = warp * 32 + lane;
+  const int64_t i0 = (int64_t)blockIdx.x * tile;
+  const int w = blockIdx.y * 32 + lane;
+  const int rows = tile + 2 * halo;
+  if (tid < K) cinv_s[tid] = lagrange_denom_inv<float, K>(tid);
+  if (warp == 0) {
+    const WalkerRec& R = walkers[w];
+    double ta = t0 + (double)i0 * dt;
+    double a = kOmegaOrb * ta;
+    double ca = cos(a), sa = sin(a);
+    double S = kAUSec * (R.k[0] * ca + R.k[1] * sa);
+    double sh = floor(S / dt);
+    shift_s[lane] = (int)sh;
+    fra_s[lane] = (float)(S / dt - sh);
+    p1_s[lane] = (float)(kAUSec * (-R.k[0] * sa + R.k[1] * ca));
+    sa_s[lane] = (float)S;
+  }
+  __syncthreads();
+  for (int ww = warp; ww < 32; ww += nw) {
+    const int64_t a0 = i0 - shift_s[ww] - halo;
+    const float2* hw = h + (int64_t)(blockIdx.y * 32 + ww) * n;
+    for (int r = lane; r < rows; r += 32) {
+      int64_t g = a0 + r;
+      winf[r * kPW + ww] = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
+    }
+  }
+  __syncthreads();
+  const MixRec& X = walkers[w].mx;
+  const float k0 = X.k[0], k1 = X.k[1], k2 = X.k[2];
+  const float u0 = X.u[0], u1 = X.u[1], u2 = X.u[2];
+  const float v0 = X.v[0], v1 = X.v[1], v2 = X.v[2];
+  const int64_t a0 = i0 - shift_s[lane] - halo;
+  const float fra = fra_s[lane], p1 = p1_s[lane], sa = sa_s[lane];
+  const float idt = (float)(1.0 / dt);
+  const float odt = (float)(kOmegaOrb * dt);
+  const float2* hw = h + (int64_t)w * n;
+  float cinv[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
+
+  // interpolate h at local row position `row0 + f` (row0 integer, f small)
+  auto interp = [&](int row0, float f, float& hp, float& hc) {
+    float fl = floorf(f);
+    float wts[K];
+    lagrange_weights<float, K>(f - fl, cinv, wts);
+    int loc = row0 + (int)fl - (K - 2) / 2;
+    float sp = 0.0f, sc = 0.0f;
+    if (loc >= 0 && loc + K <= rows) {
+#pragma unroll
+      for (int j = 0; j < K; ++j) {
+        float2 v = winf[(loc + j) * kPW + lane];
+        sp = fmaf(wts[j], v.x, sp);
+        sc = fmaf(wts[j], v.y, sc);
+      }
+    } else {
+      for (int j = 0; j < K; ++j) {
+        int64_t g = a0 + loc + j;
+        if (g >= 0 && g < n) {
+          float2 v = hw[g];
+          sp = fmaf(wts[j], v.x, sp);
+          sc = fmaf(wts[j], v.y, sc);
+        }
+      }
+    }
+    hp = sp;
+    hc = sc;
+  };
+
+  for (int s = warp; s < tile; s += nw) {
+    const int64_t i = i0 + s;
+    if (i >= n) break;
+    const OrbitRec32& O = orb[i];
+    const float d = odt * (float)s;
+    const float dS = d * p1 - 0.5f * d * d * sa;     // k.g(t) - k.g(t_a)
+    const float base_f = -fra - dS * idt;
+    float hpr[3], hcr[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float kr = k0 * O.rr[q][0] + k1 * O.rr[q][1] + k2 * O.rr[q][2];
+      interp(s + halo, base_f - kr * idt, hpr[q], hcr[q]);
+    }
+#pragma unroll
+    for (int j = 0; j < kNLink; ++j) {
+      const int rq = link_receiver(j);
+      float ks = k0 * O.rs[j][0] + k1 * O.rs[j][1] + k2 * O.rs[j][2];
+      float hps, hcs;
+      interp(s + halo - nL, base_f - rL - (O.L[j] + ks) * idt, hps, hcs);
+      float nx = O.n[j][0], ny = O.n[j][1], nz = O.n[j][2];
+      float un = u0 * nx + u1 * ny + u2 * nz;
+      float vn = v0 * nx + v1 * ny + v2 * nz;
+      float kn = k0 * nx + k1 * ny + k2 * nz;
+      float val = ((un * un - vn * vn) * (hps - hpr[rq]) + 2.0f * un * vn * (hcs - hcr[rq])) /
+                  (2.0f * (1.0f - kn));
+      if (w < W) y[((int64_t)j * n + i) * ldw + w] = val;
+    }
+  }
+}
+
+template <int K>
+cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* y,
+                     cudaStream_t s) {
+  const double dt = c->cfg.dt;
+  const int tile = 128;
+  int halo = (K / 2) + 2 +
+             (int)ceil((1.1 * kArmSec + kArmSec + kAUSec * kOmegaOrb * tile * dt) / dt);
+  int groups = (W + 31) / 32;
+  dim3 grid((unsigned)((c->n + tile - 1) / tile), (unsigned)groups);
+  dim3 block(32, 4);
+  if (c->cfg.precision == 0) {
+    size_t smem = (size_t)(tile + 2 * halo) * kPW * sizeof(double2);
+    cudaFuncSetAttribute(project_fp64_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    project_fp64_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
+                                                     c->orb64, (const double2*)h, (double*)y,
+                                                     tile, halo);
+  } else {
+    size_t smem = (size_t)(tile + 2 * halo) * kPW * sizeof(float2);
+    double q = kArmSec / dt;
+    int nL = (int)floor(q);
+    float rL = (float)(q - nL);
+    cudaFuncSetAttribute(project_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    project_mixed_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
+                                                      c->orb32, (const float2*)h, (float*)y,
+                                                      tile, halo, nL, rL);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_project(const lisa_td_ctx* c, int W, int ldw, const void* h, void* y,
+                           cudaStream_t s) {
+  switch (c->cfg.lagrange_order) {
+    case 1: return launch_k<2>(c, W, ldw, h, y, s);
+    case 3: return launch_k<4>(c, W, ldw, h, y, s);
+    case 5: return launch_k<6>(c, W, ldw, h, y, s);
+    case 7: return launch_k<8>(c, W, ldw, h, y, s);
+    case 15: return launch_k<16>(c, W, ldw, h, y, s);
+    case 31: return launch_k<32>(c, W, ldw, h, y, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace lisa

@@ -25,6 +25,9 @@ CONFIGS = {
                       channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
                       precessing=0),
     # the same physics on shorter grids (sweep / parity sizes)
+    "c2_hm_30d": dict(dt=5.0, n=518400, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
+                      channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
+                      precessing=0),
     "c2_hm_7d": dict(dt=5.0, n=120960, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=20,
                      channel_mask=7, lagrange_order=31, orbit=1, mode_mask=31,
                      precessing=0),

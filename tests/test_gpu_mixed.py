@@ -1,0 +1,161 @@
+"""Parity of the mixed-precision GPU path (FP32 arithmetic, double-float
+phase/time, FP64 anchors) with the FP64 oracle.  Bars: 1e-4 norm-relative on
+series; |dlogL| <= 0.05 for posterior-bulk walkers (logL >= -100) at SNR 2000,
+and 1e-4 relative for far walkers (|logL| >> 1, where an absolute 0.05 is
+below FP32 resolution)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import likelihood, pipeline, response
+from paper_2501_08261_gb300 import api, workloads
+
+from helpers import gpu_kwargs, norm_rel, oracle_setup
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+torch = pytest.importorskip("torch")
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2501_08261_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def _lik(cfg, W):
+    return api.Likelihood(precision=1, max_walkers=W, **gpu_kwargs(cfg))
+
+
+def _walkers(cfg, w, seed):
+    return workloads.prior_draws(w, cfg["n"], cfg["dt"], seed,
+                                 precessing=bool(cfg["precessing"]), logm=(5.5, 7.0))
+
+
+CONFIGS = ["c1_fp64_1d", "c2_hm_1d", "c3_prec_1d"]
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_mixed_waveform(name):
+    cfg = workloads.config(name)
+    th = _walkers(cfg, 3, 11)
+    h = _lik(cfg, 3).waveform(_t(th)).cpu().numpy()
+    s = oracle_setup(cfg)
+    for w in range(3):
+        hp, hc = pipeline.polarizations(th[w], s)
+        assert norm_rel(h[w, :, 0], hp) < 1e-5, w
+        assert norm_rel(h[w, :, 1], hc) < 1e-5, w
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_mixed_projection(name):
+    cfg = workloads.config(name)
+    th = _walkers(cfg, 2, 12)
+    y = _lik(cfg, 2).project(_t(th)).cpu().numpy()
+    s = oracle_setup(cfg)
+    for w in range(2):
+        hp, _ = pipeline.polarizations(th[w], s)
+        yo = pipeline.links(th[w], s)
+        for j, l in enumerate((1, 2, 3, -1, -2, -3)):
+            # y is a difference of two interpolated h values: its rounding error
+            # scales with |h|, so the bar is relative to max(|y|, 1e-2 |h|)
+            scale = max(np.max(np.abs(yo[l])), 1e-2 * np.max(np.abs(hp)))
+            assert np.max(np.abs(y[j, :, w] - yo[l])) <= TOL * scale, (w, l)
+
+
+@pytest.mark.parametrize("gen,orbit", [(15, 0), (20, 1)])
+def test_mixed_tdi_of_oracle_links(gen, orbit):
+    cfg = workloads.config("c1_fp64_1d", tdi_gen=gen, orbit=orbit, n=4320)
+    s = oracle_setup(cfg)
+    rng = np.random.default_rng(5)
+    W = 70                                        # two CTA walker blocks, ragged
+    y = np.zeros((6, cfg["n"], W))
+    for w in range(W):
+        for j in range(6):
+            y[j, :, w] = np.convolve(rng.normal(size=cfg["n"]), np.hanning(25), mode="same")
+    aet = _lik(cfg, W).tdi(torch.as_tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
+    for w in (0, 1, 33, 63, 64, 69):
+        yd = {l: y[j, :, w] for j, l in enumerate((1, 2, 3, -1, -2, -3))}
+        X, Y, Z = response.tdi_xyz(yd, cfg["n"], 0.0, cfg["dt"], s.orbit, gen, 31)
+        want = response.aet_from_xyz(X, Y, Z)
+        for c in range(3):
+            assert norm_rel(aet[c, :, w], want[c]) < TOL, (w, c)
+
+
+def _snr_scaled(truth, s, snr):
+    d = pipeline.aet(truth, s)
+    rho = math.sqrt(-2 * likelihood.loglike(np.zeros_like(d), d, s.dt, s.f_lo, s.f_hi,
+                                            s.tdi_gen, s.channel_mask))
+    th = truth.copy()
+    th[8] *= rho / snr
+    return th, d * (snr / rho)
+
+
+@pytest.mark.parametrize("name", CONFIGS)
+def test_mixed_loglike_bulk_and_far(name):
+    cfg = workloads.config(name)
+    s = oracle_setup(cfg)
+    truth = _walkers(cfg, 1, 21)[0]
+    truth, d = _snr_scaled(truth, s, 2000.0)
+    z = workloads.standard_normals(8, 15, 23)
+    th = np.repeat(truth[None], 9, axis=0)
+    scales = {8: 2e-3, 11: 2e-4, 12: 2e-4, 14: 0.2, 0: 2e-5, 9: 1e-3, 13: 1e-3}
+    for w in range(1, 9):
+        for p, sc in scales.items():
+            th[w, p] += (sc * z[w - 1, p] * th[w, p]) if p in (0, 8) else sc * z[w - 1, p]
+    th[8, 12] += 0.05                              # a far walker
+    lk = _lik(cfg, 9)
+    lk.set_data(_t(d))
+    got = lk.loglike(_t(th)).cpu().numpy()
+    want = np.array([pipeline.loglike(t, s, d) for t in th])
+    for g, o in zip(got, want):
+        if o >= -100.0:
+            assert abs(g - o) <= 0.05, (g, o)
+        else:
+            assert abs(g - o) <= 1e-4 * abs(o), (g, o)
+    assert abs(got[0]) <= 0.05
+
+
+def test_mixed_full_size_sampled_outputs():
+    cfg = workloads.config("c2_hm_60d")
+    s = oracle_setup(cfg)
+    th = _walkers(cfg, 2, 60)
+    lk = _lik(cfg, 2)
+    aet = lk.tdi(lk.project(_t(th))).cpu().numpy()
+    idx = np.unique(np.concatenate([np.arange(0, 40), np.arange(cfg["n"] - 40, cfg["n"]),
+                                    np.random.default_rng(3).integers(0, cfg["n"], 220)]))
+    for w in range(2):
+        want = pipeline.aet(th[w], s, idx=idx)
+        scale = np.max(np.abs(aet[:, :, w]))
+        for c in range(3):
+            assert np.max(np.abs(aet[c, idx, w] - want[c])) <= TOL * scale, (w, c)
+
+
+def test_mixed_matches_fp64_gpu_at_bench_shape():
+    """60 d, 5 mode pairs, Keplerian TDI-2, 64 walkers: mixed vs FP64 GPU logL
+    (both against the same injection at SNR ~ 2000)."""
+    cfg = workloads.config("c2_hm_60d")
+    W = 64
+    th = _walkers(cfg, W, 70)
+    lk64 = api.Likelihood(precision=0, max_walkers=W, **gpu_kwargs(cfg))
+    lk32 = _lik(cfg, W)
+    s = oracle_setup(cfg)
+    truth, d = _snr_scaled(th[0], s, 2000.0)
+    th[0] = truth
+    th[1:8] = truth
+    th[1:8, 14] += np.linspace(-1.0, 1.0, 7)       # bulk walkers near the injection
+    for lk in (lk64, lk32):
+        lk.set_data(_t(d))
+    a = lk64.loglike(_t(th)).cpu().numpy()
+    b = lk32.loglike(_t(th)).cpu().numpy()
+    for g, o in zip(b, a):
+        if o >= -100.0:
+            assert abs(g - o) <= 0.05, (g, o)
+        else:
+            assert abs(g - o) <= 1e-4 * abs(o), (g, o)
