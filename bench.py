@@ -153,7 +153,7 @@ def cpu_baseline(cfg, theta, data_np, seconds_budget=20.0):
 def _inject(torch, api, lk_ref, lk_all, params, n, snr=2000.0):
     """Zero-noise data: the response of walker 0 scaled to the given SNR; the
     walker's distance is rescaled to match and walkers 1..7 sit near it."""
-    aet = lk_ref.tdi(lk_ref.project(params[:1])).reshape(3, n).contiguous()
+    aet = lk_ref.tdi(lk_ref.project(params[:1])).reshape(3, n).to(torch.float64).contiguous()
     lk_ref.set_data(aet)
     far = params[:1].clone()
     far[0, 8] = 1e30                                   # h -> 0: logL = -(d|d)/2
@@ -226,7 +226,7 @@ def run_ours(args):
 
     def step_e2e():
         dparams.copy_(host_params, non_blocking=True)
-        api.lisa_td_loglike_batch(lk32.ctx, dparams, W, logl, None, stream)
+        api.lisa_td_loglike_batch(lk32.ctx, dparams, W, logl, None, stream)  # validated above
         host_logl.copy_(logl, non_blocking=True)
 
     ms_e2e = float("nan")

@@ -141,6 +141,20 @@ def lisa_td_destroy(ctx):
     lib().lisa_td_destroy(ctx)
 
 
+def _need(t, dtype, shape, what):
+    """Validate a tensor before its pointer crosses the C ABI (which cannot check
+    element type or size): dtype, exact shape, CUDA device, contiguity."""
+    if t.dtype != dtype:
+        raise TypeError(f"{what}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_cuda:
+        raise ValueError(f"{what}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: must be contiguous")
+    return t
+
+
 class Likelihood:
     """Owns one context; tensors in, tensors out (torch on cuda)."""
 
@@ -162,30 +176,40 @@ class Likelihood:
         except Exception:
             pass
 
+    def _params(self, params):
+        params = params.to(self.torch.float64).contiguous()
+        return _need(params, self.torch.float64, (params.shape[0], 15), "params")
+
     def set_data(self, aet):
-        lisa_td_set_data(self.ctx, aet.contiguous())
+        aet = aet.to(self.torch.float64).contiguous()
+        lisa_td_set_data(self.ctx, _need(aet, self.torch.float64, (3, self.cfg.n), "data"))
 
     def waveform(self, params):
+        params = self._params(params)
         W = params.shape[0]
         h = self.torch.empty((W, self.cfg.n, 2), dtype=self.dtype, device=params.device)
-        lisa_td_waveform(self.ctx, params.contiguous(), W, h)
+        lisa_td_waveform(self.ctx, params, W, h)
         return h
 
     def project(self, params):
+        params = self._params(params)
         W = params.shape[0]
         y = self.torch.empty((6, self.cfg.n, W), dtype=self.dtype, device=params.device)
-        lisa_td_project(self.ctx, params.contiguous(), W, y)
+        lisa_td_project(self.ctx, params, W, y)
         return y
 
     def tdi(self, y):
+        y = y.contiguous()
         W = y.shape[2]
+        _need(y, self.dtype, (6, self.cfg.n, W), "y")
         aet = self.torch.empty((3, self.cfg.n, W), dtype=self.dtype, device=y.device)
-        lisa_td_tdi(self.ctx, y.contiguous(), W, aet)
+        lisa_td_tdi(self.ctx, y, W, aet)
         return aet
 
     def loglike(self, params, with_status=False):
+        params = self._params(params)
         W = params.shape[0]
         out = self.torch.empty(W, dtype=self.torch.float64, device=params.device)
         st = self.torch.empty(W, dtype=self.torch.int32, device=params.device)
-        lisa_td_loglike_batch(self.ctx, params.contiguous(), W, out, st)
+        lisa_td_loglike_batch(self.ctx, params, W, out, st)
         return (out, st) if with_status else out

@@ -42,7 +42,7 @@ void free_ctx(lisa_td_ctx* c) {
   }
   void* ptrs[] = {c->orb64, c->orb32, c->psdw, c->plan.tw_n, c->plan.tw1, c->plan.tw2,
                   c->tdi_tab, c->chan_list, c->data64, c->data32, c->walkers, c->h, c->y,
-                  c->r, c->fy, c->partial, c->status};
+                  c->r, c->fy, c->partial, c->status, c->tdi_tiles};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -119,6 +119,7 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
       {(void**)&c->fy, (size_t)c->esize * 3 * n * W},
       {(void**)&c->partial, sizeof(double) * 3 * (c->plan.n1 / 2 + 1) * W},
       {(void**)&c->status, sizeof(int32_t) * W},
+      {(void**)&c->tdi_tiles, sizeof(lisa::TdiTileTerm) * ((n + lisa::kTdiTile - 1) / lisa::kTdiTile) * 42},
   };
   for (auto& a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -131,6 +132,7 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
   }
   lisa::TdiTable tab = lisa::build_tdi_table(cfg->tdi_gen);
   c->tdi_nd = tab.max_links_in_delay;
+  c->n_dterms = tab.n_dterms;
   int chans[3] = {0, 0, 0}, nch = 0;
   for (int q = 0; q < 3; ++q)
     if ((cfg->channel_mask >> q) & 1) chans[nch++] = q;
@@ -141,6 +143,7 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
   if (e == cudaSuccess) e = lisa::launch_orbit_tables(c, s);
   if (e == cudaSuccess) e = lisa::launch_psd_weights(c, s);
   if (e == cudaSuccess) e = lisa::launch_twiddles(c, s);
+  if (e == cudaSuccess) e = lisa::launch_tdi_tiles(c, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_ctx(c);

@@ -121,7 +121,31 @@ struct TdiTerm {
 struct TdiTable {
   int nterm[kNLink];              // terms that read link l (4 for TDI 1.5, 8 for TDI 2)
   TdiTerm term[kNLink][8];
+  int8_t dterm[kNLink][8];        // index among the delayed terms, -1 if undelayed
+  int n_dterms;
   int max_links_in_delay;
+};
+
+// ---- mixed-path TDI weights, per 64-sample tile and delayed term ------------
+// Built once per context from the FP64 orbit table.  For a tile starting at
+// sample i_a and a term of delay D(t): tau = i - D(t)/dt; the tile anchor
+// tau_a = i_a - D(t_a)/dt = i_a + bo + eps_a.  With c = i + bo and first
+// differences dy_m = y_{m+1} - y_m, the Lagrange value at eps_a is rewritten
+// (summation by parts, exact) as
+//   y_c + sum_{m=-15..15} C_m dy_{c+m},  C_m = sum_{o_k > m} w_k (m >= 0),
+//                                        C_m = -sum_{o_k <= m} w_k (m < 0),
+// with C the FP64 cumulative weights rounded to FP32.  Inside the tile the
+// fraction drifts by j (a1 + j a2) samples (j = i - i_a); m1 = sum (C_f - C)
+// is the first-moment error of the rounding.  The kernel evaluates
+//   y_c + sum_m C_m dy_{c+m} + (j (a1 + j a2) - m1) dy_c.
+constexpr int kTdiTile = 64;
+struct TdiTileTerm {
+  float C[32];           // C[m + H], m = -H .. H (H = (K-2)/2); C[K-1..31] = 0
+  float m1, a1, a2;
+  float eps_a;
+  int bo;
+  int split;             // the fraction leaves [0, 1) inside the tile
+  int pad[2];
 };
 
 // ---- small helpers --------------------------------------------------------

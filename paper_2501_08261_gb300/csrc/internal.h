@@ -34,6 +34,8 @@ struct lisa_td_ctx {
   lisa::TdiTable* tdi_tab;         // device copy of the TDI term table
   int tdi_nd;                      // most light times in one delay
   int* chan_list;                  // device [3]: indices of the channels in the mask
+  lisa::TdiTileTerm* tdi_tiles;    // mixed path: [n / 64 tiles][delayed terms]
+  int n_dterms;                    // delayed terms (18 for TDI 1.5, 42 for TDI 2)
   double* data64;                  // [3][n]
   float* data32;                   // [3][n]
   int has_data;
@@ -76,5 +78,6 @@ cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl,
                           int32_t* status, cudaStream_t s);
 int plan_fft(int64_t n, FftPlan* p);
 TdiTable build_tdi_table(int gen);
+cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s);
 
 }  // namespace lisa

@@ -59,6 +59,10 @@ TdiTable build_tdi_table(int gen) {
       if (X[q].nd > T.max_links_in_delay) T.max_links_in_delay = X[q].nd;
     }
   }
+  T.n_dterms = 0;
+  for (int j = 0; j < kNLink; ++j)
+    for (int q = 0; q < 8; ++q)
+      T.dterm[j][q] = (q < T.nterm[j] && T.term[j][q].ndelay > 0) ? (int8_t)T.n_dterms++ : -1;
   return T;
 }
 
@@ -158,153 +162,291 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
   }
 }
 
-// Mixed path.  One CTA = 64 walkers (each lane holds walkers 2l, 2l+1) x 64
-// output samples (4 warps x 16 consecutive samples).  Per link the y window is
-// staged in shared memory; per term the CTA computes the walker-independent
-// Lagrange weights of its 64 samples once (delay D = n_L L0 + sum cnt dL(t),
-// the n_L L0 / dt part split exactly into integer + fraction), and each thread
-// applies them to its 16 samples x 2 walkers with a 16-row sliding register
-// window (one new shared-memory row per tap).
-constexpr int kMixTile = 64;
-constexpr int kMixSpt = 16;
-constexpr int kPW2 = 33;                 // padded walker pairs per row
+// ---------------------------------------------------------------------------
+// Mixed path.
+//
+// TDI cancels the signal by ~(2 pi f L)^2 (X, A, E) and up to ~(2 pi f L)^4
+// (T of TDI 2) at low frequency, so any *systematic* per-term error -- FP32
+// rounding of Lagrange weights that stay constant while the delay drifts
+// slowly, or of the fractional delay itself -- leaks through where the PSD
+// weights are largest.  The delays depend only on the orbit, so their weights
+// are tabulated once per context in FP64 (tdi_tiles_kernel): per 64-sample
+// tile and delayed term, FP32-rounded weights at the tile anchor, the exact
+// DC gain of those rounded weights, the first moment of their rounding error,
+// and a quadratic for the drift of the fraction inside the tile.  The kernel
+// applies the constant tile weights as an FIR plus the two one-tap corrections
+// (see TdiTileTerm), so its remaining errors are FP32 rounding of the samples
+// themselves, which is white and harmless.
+// ---------------------------------------------------------------------------
 
-// acc[r] += sum_m wts[m][s0 + r] * y[row(r) + m] for the thread's 16 samples
-template <int K>
-__device__ __forceinline__ void apply_term(float2 (&acc)[kMixSpt], const float2* __restrict__ yw,
-                                           const float* __restrict__ wts, const int* base_s,
-                                           int s0, int b0, bool slide, int rows, int lane) {
-  if (slide) {
-    float2 win[kMixSpt];
-#pragma unroll
-    for (int r = 0; r < kMixSpt; ++r) win[r] = yw[(b0 + r) * kPW2 + lane];
-#pragma unroll
+__device__ void lagrange_weights_f64(double eps, int K, double* w) {
+  const int H = (K - 2) / 2;
+  for (int j = 0; j < K; ++j) {
+    double num = 1.0, den = 1.0;
     for (int m = 0; m < K; ++m) {
-      float wk[kMixSpt];
-#pragma unroll
-      for (int r4 = 0; r4 < kMixSpt; r4 += 4) {
-        float4 t4 = *reinterpret_cast<const float4*>(&wts[m * kMixTile + s0 + r4]);
-        wk[r4] = t4.x; wk[r4 + 1] = t4.y; wk[r4 + 2] = t4.z; wk[r4 + 3] = t4.w;
-      }
-#pragma unroll
-      for (int r = 0; r < kMixSpt; ++r) {
-        acc[r].x = fmaf(wk[r], win[r].x, acc[r].x);
-        acc[r].y = fmaf(wk[r], win[r].y, acc[r].y);
-      }
-      if (m + 1 < K) {
-#pragma unroll
-        for (int r = 0; r < kMixSpt - 1; ++r) win[r] = win[r + 1];
-        win[kMixSpt - 1] = yw[(b0 + kMixSpt + m) * kPW2 + lane];
-      }
+      if (m == j) continue;
+      num *= eps - (double)(m - H);
+      den *= (double)(j - m);
     }
-  } else {                                         // rare: a stencil jump inside the run
-#pragma unroll
-    for (int r = 0; r < kMixSpt; ++r) {
-      const int b = base_s[s0 + r];
-      for (int m = 0; m < K; ++m) {
-        int row = b + m;
-        float2 v = (row >= 0 && row < rows) ? yw[row * kPW2 + lane] : make_float2(0.0f, 0.0f);
-        float wv = wts[m * kMixTile + s0 + r];
-        acc[r].x = fmaf(wv, v.x, acc[r].x);
-        acc[r].y = fmaf(wv, v.y, acc[r].y);
-      }
-    }
+    w[j] = num / den;
   }
 }
 
-__device__ __forceinline__ void add_scaled(float2 (&dst)[kMixSpt], const float2 (&src)[kMixSpt],
+__device__ inline double term_delay(const TdiTerm& T, const OrbitRec64& O) {
+  double D = 0.0;
+  for (int l = 0; l < kNLink; ++l) D += (double)T.cnt[l] * O.L[l];
+  return D;
+}
+
+__global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
+                                 const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
+                                 int ntiles, TdiTileTerm* __restrict__ out) {
+  const int nd = tab->n_dterms;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)ntiles * nd) return;
+  const int tile = (int)(id / nd), d = (int)(id % nd);
+  int jl = 0, q = 0;
+  for (int j = 0; j < kNLink; ++j)
+    for (int qq = 0; qq < tab->nterm[j]; ++qq)
+      if (tab->dterm[j][qq] == d) { jl = j; q = qq; }
+  const TdiTerm T = tab->term[jl][q];
+  const int64_t ia = (int64_t)tile * kTdiTile;
+  auto tau_rel = [&](int j) -> double {          // tau(i) - i at i = ia + j
+    int64_t i = ia + j < n ? ia + j : n - 1;
+    return -term_delay(T, orb[i]) / dt;
+  };
+  const double ta = tau_rel(0);
+  const double fl = floor(ta);
+  const double eps = ta - fl;
+  TdiTileTerm R;
+  R.bo = (int)fl;
+  R.eps_a = (float)eps;
+  // quadratic drift through j = 0, 32, 63
+  const double d32 = tau_rel(32) - ta, d63 = tau_rel(63) - ta;
+  const double a2 = (d63 / 63.0 - d32 / 32.0) / (63.0 - 32.0);
+  const double a1 = d32 / 32.0 - a2 * 32.0;
+  R.a1 = (float)a1;
+  R.a2 = (float)a2;
+  int split = 0;
+  for (int j = 0; j < kTdiTile; ++j) {
+    double e = eps + (tau_rel(j) - ta);
+    if (e < 0.0 || e >= 1.0) split = 1;
+  }
+  R.split = split;
+  double w[32];
+  lagrange_weights_f64(eps, K, w);
+  const int H = (K - 2) / 2;                       // node offsets o_k = k - H, k = 0..K-1
+  double mom = 0.0;
+  for (int q = 0; q < 32; ++q) R.C[q] = 0.0f;
+  for (int mi = 0; mi < K - 1; ++mi) {             // m = mi - H, from -H to H
+    const int m = mi - H;
+    double c = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const int o = k - H;
+      if (m >= 0 && o > m) c += w[k];
+      if (m < 0 && o <= m) c -= w[k];
+    }
+    const float cf = (float)c;
+    R.C[mi] = cf;
+    mom += (double)cf - c;
+  }
+  R.m1 = (float)mom;
+  R.pad[0] = R.pad[1] = 0;
+  out[id] = R;
+}
+
+constexpr int kMixTile = kTdiTile;
+constexpr int kMixSpt = 8;                  // samples per thread (8 warps x 8 = 64)
+constexpr int kPW2 = 33;                 // padded walkers per row
+
+__device__ __forceinline__ void add_scaled(float (&dst)[kMixSpt], const float (&src)[kMixSpt],
                                            float sg) {
 #pragma unroll
   for (int r = 0; r < kMixSpt; ++r) {
-    dst[r].x = fmaf(sg, src[r].x, dst[r].x);
-    dst[r].y = fmaf(sg, src[r].y, dst[r].y);
+    dst[r] = fmaf(sg, src[r], dst[r]);
   }
 }
 
-template <int K>
-__global__ void __launch_bounds__(128) tdi_mixed_kernel(
-    const TdiTable* __restrict__ tab, int W, int ldw, int64_t n, double dt,
-    const OrbitRec32* __restrict__ orb, const float* __restrict__ y, float* __restrict__ out,
-    const float* __restrict__ data, int resid, int hl, int hr) {
-  extern __shared__ float2 yw[];                   // [(64 + hl + hr)][kPW2]
-  __shared__ __align__(16) float wts_s[K][kMixTile];
-  __shared__ int base_s[kMixTile];
-  __shared__ float cinv_s[K];
-  const int lane = threadIdx.x, warp = threadIdx.y;
-  const int tid = warp * 32 + lane;
-  const int64_t i0 = (int64_t)blockIdx.x * kMixTile;
-  const int wa = blockIdx.y * 64 + 2 * lane;       // walkers wa, wa + 1
-  const int rows = kMixTile + hl + hr;
-  const int s0 = warp * kMixSpt;
-  if (tid < K) cinv_s[tid] = lagrange_denom_inv<float, K>(tid);
-  float2 ax[kMixSpt], ay[kMixSpt], az[kMixSpt];
+// small[r] += sg * (sum_{m'} C[m'] dy[b0 + r + m'] + (j (a1 + j a2) - m1) dy[b0 + r + H])
+// (the centre sample y_c is accumulated separately by the caller)
+template <int K, int SPT>
+__device__ __forceinline__ void apply_tile_term(float (&acc)[SPT], const float* __restrict__ dyw,
+                                                const TdiTileTerm* __restrict__ P, float sg,
+                                                int s0, int b0, int lane) {
+  constexpr int H = (K - 2) / 2;
+  constexpr int NT = K - 1;                       // taps on the differences
+  float c[NT];
 #pragma unroll
-  for (int r = 0; r < kMixSpt; ++r) ax[r] = ay[r] = az[r] = make_float2(0.0f, 0.0f);
-  const double q0 = kArmSec / dt;
+  for (int k = 0; k < NT; ++k) c[k] = sg * P->C[k];
+  const float m1 = P->m1, a1 = P->a1, a2 = P->a2;
+  float win[SPT];
+#pragma unroll
+  for (int r = 0; r < SPT; ++r) win[r] = dyw[(b0 + r) * kPW2 + lane];
+#pragma unroll
+  for (int m = 0; m < NT; ++m) {
+#pragma unroll
+    for (int r = 0; r < SPT; ++r) {
+      acc[r] = fmaf(c[m], win[r], acc[r]);
+    }
+    if (m == H) {                                 // win[r] = dy at the centre
+#pragma unroll
+      for (int r = 0; r < SPT; ++r) {
+        const float jj = (float)(s0 + r);
+        const float dr = sg * (jj * fmaf(jj, a2, a1) - m1);
+        acc[r] = fmaf(dr, win[r], acc[r]);
+      }
+    }
+    if (m + 1 < NT) {
+#pragma unroll
+      for (int r = 0; r < SPT - 1; ++r) win[r] = win[r + 1];
+      win[SPT - 1] = dyw[(b0 + SPT + m) * kPW2 + lane];
+    }
+  }
+}
+
+// tiles whose fraction wraps inside the tile (rare): per-sample FP32 weights,
+// still as y_c' + sum w_k (y_k - y_c') so that their DC error meets only differences
+template <int K>
+__device__ __noinline__ void split_one(const float* __restrict__ yw,
+                                       const TdiTileTerm* __restrict__ P, int s, int hl,
+                                       int rows, int lane, float& yc_out, float& small_out) {
+  const int H = (K - 2) / 2;
+  const float jj = (float)s;
+  float e = P->eps_a + jj * fmaf(jj, P->a2, P->a1);
+  float fl = floorf(e);
+  float eps = e - fl;
+  const int c = s + hl + P->bo + (int)fl;
+  const float yc = (c >= 0 && c < rows) ? yw[c * kPW2 + lane] : 0.0f;
+  float ax = 0.0f;
+  for (int k = 0; k < K; ++k) {
+    float num = 1.0f, den = 1.0f;
+    for (int m = 0; m < K; ++m) {
+      if (m == k) continue;
+      num *= eps - (float)(m - H);
+      den *= (float)(k - m);
+    }
+    const float wk = num / den;
+    const int row = c + k - H;
+    float v = (row >= 0 && row < rows) ? yw[row * kPW2 + lane] : 0.0f;
+    ax = fmaf(wk, v - yc, ax);
+  }
+  yc_out = yc;
+  small_out = ax;
+}
+
+// compensated (Knuth two-sum) accumulation of the |y|-sized centre samples:
+// hi + lo keeps their sum exact to ~2^-48, so that the TDI cancellation in
+// X, Y, Z (and further in T) is not limited by FP32 rounding of these sums
+template <int SPT>
+__device__ __forceinline__ void add_rows(float (&hi)[SPT], float (&lo)[SPT],
+                                         const float* __restrict__ yw, int row0, float sg,
+                                         int lane) {
+#pragma unroll
+  for (int r = 0; r < SPT; ++r) {
+    const float v = sg * yw[(row0 + r) * kPW2 + lane];
+    const float s = hi[r] + v;
+    const float bb = s - hi[r];
+    lo[r] += (hi[r] - (s - bb)) + (v - bb);
+    hi[r] = s;
+  }
+}
+template <int SPT>
+__device__ __forceinline__ void add_vals(float (&hi)[SPT], float (&lo)[SPT], const float (&src)[SPT],
+                                         float sg) {
+#pragma unroll
+  for (int r = 0; r < SPT; ++r) {
+    const float v = sg * src[r];
+    const float s = hi[r] + v;
+    const float bb = s - hi[r];
+    lo[r] += (hi[r] - (s - bb)) + (v - bb);
+    hi[r] = s;
+  }
+}
+
+// Accumulators: `main` holds the |y|-sized centre samples of every term, `small`
+// the difference FIRs and corrections; X = main + small only at the end, where
+// the TDI cancellation has made X small.
+template <int K>
+__global__ void __launch_bounds__(32 * (kMixTile / kMixSpt), 2) tdi_mixed_kernel(
+    const TdiTable* __restrict__ tab, const TdiTileTerm* __restrict__ tiles, int W, int ldw,
+    int64_t n, const float* __restrict__ y, float* __restrict__ out,
+    const float* __restrict__ data, int resid, int hl, int hr) {
+  constexpr int SPT = kMixSpt;
+  constexpr int NWP = kMixTile / kMixSpt;
+  extern __shared__ float smem2[];
+  const int rows = kMixTile + hl + hr;
+  float* yw = smem2;                              // [rows][kPW2]
+  float* dyw = smem2 + rows * kPW2;               // [rows][kPW2], dy_r = y_{r+1} - y_r
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * kMixTile;
+  const int w = blockIdx.y * 32 + lane;
+  const int s0 = warp * SPT;
+  const int nd = tab->n_dterms;
+  const TdiTileTerm* tt = tiles + (int64_t)blockIdx.x * nd;
+  float mx[SPT], my[SPT], mz[SPT], sx[SPT], sy[SPT], sz[SPT];   // main (hi) and small
+#pragma unroll
+  for (int r = 0; r < SPT; ++r)
+    mx[r] = my[r] = mz[r] = sx[r] = sy[r] = sz[r] = 0.0f;
 
   for (int j = 0; j < kNLink; ++j) {
     __syncthreads();
-    for (int r = warp; r < rows; r += 4) {
+    for (int r = warp; r < rows; r += NWP) {
       int64_t g = i0 - hl + r;
-      float2 v = make_float2(0.0f, 0.0f);
-      if (g >= 0 && g < n) {
-        const float* src = y + ((int64_t)j * n + g) * ldw;
-        if (wa < W) v.x = src[wa];
-        if (wa + 1 < W) v.y = src[wa + 1];
-      }
+      float v = 0.0f;
+      if (g >= 0 && g < n && w < W) v = y[((int64_t)j * n + g) * ldw + w];
       yw[r * kPW2 + lane] = v;
     }
+    __syncthreads();
+    for (int r = warp; r < rows; r += NWP) {
+      float a = yw[r * kPW2 + lane];
+      float b = r + 1 < rows ? yw[(r + 1) * kPW2 + lane] : a;
+      dyw[r * kPW2 + lane] = b - a;
+    }
+    __syncthreads();
     const int nt = tab->nterm[j];
     for (int q = 0; q < nt; ++q) {
       const TdiTerm T = tab->term[j][q];
       const float sg = (float)T.sign;
-      if (T.ndelay > 0) {
-        __syncthreads();                           // previous term done with wts_s
-        if (tid < kMixTile) {
-          const int64_t i = i0 + tid;
-          double qd = q0 * (double)T.ndelay;
-          double nd = floor(qd);
-          float f = -(float)(qd - nd);
-          if (i < n) {
-            const float* L = orb[i].L;
-            float dsum = 0.0f;
-#pragma unroll
-            for (int l = 0; l < kNLink; ++l) dsum = fmaf((float)T.cnt[l], L[l], dsum);
-            f -= dsum * (float)(1.0 / dt);
-          }
-          float fl = floorf(f);
-          float w[K];
-          float ci[K];
-#pragma unroll
-          for (int m = 0; m < K; ++m) ci[m] = cinv_s[m];
-          lagrange_weights<float, K>(f - fl, ci, w);
-#pragma unroll
-          for (int m = 0; m < K; ++m) wts_s[m][tid] = sg * w[m];
-          // first staged row read by sample tid
-          base_s[tid] = tid + hl - (int)nd + (int)fl - (K - 2) / 2;
-        }
-      }
-      __syncthreads();
       if (T.ndelay == 0) {
-        float2 acc0[kMixSpt];
-#pragma unroll
-        for (int r = 0; r < kMixSpt; ++r) acc0[r] = yw[(s0 + r + hl) * kPW2 + lane];
-        if (T.chan == 0) add_scaled(ax, acc0, sg);
-        else if (T.chan == 1) add_scaled(ay, acc0, sg);
-        else add_scaled(az, acc0, sg);
+        if (T.chan == 0) add_rows<SPT>(mx, sx, yw, s0 + hl, sg, lane);
+        else if (T.chan == 1) add_rows<SPT>(my, sy, yw, s0 + hl, sg, lane);
+        else add_rows<SPT>(mz, sz, yw, s0 + hl, sg, lane);
         continue;
       }
-      const int b0 = base_s[s0];
-      const bool slide = (base_s[s0 + kMixSpt - 1] == b0 + kMixSpt - 1) && b0 >= 0 &&
-                         b0 + kMixSpt - 1 + K <= rows;
-      if (T.chan == 0) apply_term<K>(ax, yw, &wts_s[0][0], base_s, s0, b0, slide, rows, lane);
-      else if (T.chan == 1) apply_term<K>(ay, yw, &wts_s[0][0], base_s, s0, b0, slide, rows, lane);
-      else apply_term<K>(az, yw, &wts_s[0][0], base_s, s0, b0, slide, rows, lane);
+      const TdiTileTerm* P = tt + tab->dterm[j][q];
+      if (!P->split) {
+        const int c0 = s0 + hl + P->bo;            // centre row of sample s0
+        const int b0 = c0 - (K - 2) / 2;
+        if (T.chan == 0) {
+          add_rows<SPT>(mx, sx, yw, c0, sg, lane);
+          apply_tile_term<K, SPT>(sx, dyw, P, sg, s0, b0, lane);
+        } else if (T.chan == 1) {
+          add_rows<SPT>(my, sy, yw, c0, sg, lane);
+          apply_tile_term<K, SPT>(sy, dyw, P, sg, s0, b0, lane);
+        } else {
+          add_rows<SPT>(mz, sz, yw, c0, sg, lane);
+          apply_tile_term<K, SPT>(sz, dyw, P, sg, s0, b0, lane);
+        }
+      } else {
+        float ycv[SPT], smv[SPT];
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) split_one<K>(yw, P, s0 + r, hl, rows, lane, ycv[r], smv[r]);
+        if (T.chan == 0) {
+          add_vals<SPT>(mx, sx, ycv, sg);
+          add_scaled(sx, smv, sg);
+        } else if (T.chan == 1) {
+          add_vals<SPT>(my, sy, ycv, sg);
+          add_scaled(sy, smv, sg);
+        } else {
+          add_vals<SPT>(mz, sz, ycv, sg);
+          add_scaled(sz, smv, sg);
+        }
+      }
     }
   }
   const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f, r3 = 0.57735026918962576f;
 #pragma unroll
-  for (int r = 0; r < kMixSpt; ++r) {
+  for (int r = 0; r < SPT; ++r) {
     const int64_t i = i0 + s0 + r;
     if (i >= n) continue;
     float dA = 0.0f, dE = 0.0f, dT = 0.0f;
@@ -313,15 +455,20 @@ __global__ void __launch_bounds__(128) tdi_mixed_kernel(
       dE = data[n + i];
       dT = data[2 * n + i];
     }
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int w = wa + e;
-      if (w >= W) continue;
-      float X = e ? ax[r].y : ax[r].x, Y = e ? ay[r].y : ay[r].x, Z = e ? az[r].y : az[r].x;
-      out[(0 * n + i) * ldw + w] = (Z - X) * r2 - dA;
-      out[(1 * n + i) * ldw + w] = (X - 2.0f * Y + Z) * r6 - dE;
-      out[(2 * n + i) * ldw + w] = (X + Y + Z) * r3 - dT;
-    }
+    if (w >= W) continue;
+    // A, E, T from the main (hi) parts combined error-free first, the small
+    // parts after: T = (X + Y + Z)/sqrt3 cancels the signal further still
+    df32 zx = two_sum(mz[r], -mx[r]);
+    df32 xy = two_sum(mx[r], -2.0f * my[r]);
+    df32 xyz = two_sum(xy.hi, mz[r]);
+    df32 xy3 = two_sum(mx[r], my[r]);
+    df32 t3 = two_sum(xy3.hi, mz[r]);
+    const float A = zx.hi + (zx.lo + (sz[r] - sx[r]));
+    const float E = xyz.hi + ((xy.lo + xyz.lo) + (sx[r] - 2.0f * sy[r] + sz[r]));
+    const float Tt = t3.hi + ((xy3.lo + t3.lo) + (sx[r] + sy[r] + sz[r]));
+    out[(0 * n + i) * ldw + w] = A * r2 - dA;
+    out[(1 * n + i) * ldw + w] = E * r6 - dE;
+    out[(2 * n + i) * ldw + w] = Tt * r3 - dT;
   }
 }
 
@@ -344,13 +491,14 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
         c->tdi_tab, W, ldw, ldw, c->n, dt, c->orb64, (const double*)y, (double*)out, c->data64,
         resid, hl, hr);
   } else {
-    int hlm = (int)ceil(nd * (kArmSec / dt + 0.02)) + K / 2 + 3;
+    int hlm = (int)ceil(nd * 1.1 * kArmSec / dt) + K / 2 + 3;
     int hrm = K / 2 + 2;
-    size_t smem = (size_t)(kMixTile + hlm + hrm) * kPW2 * sizeof(float2);
-    dim3 gridm((unsigned)((c->n + kMixTile - 1) / kMixTile), (unsigned)((W + 63) / 64));
+    size_t smem = (size_t)2 * (kMixTile + hlm + hrm) * kPW2 * sizeof(float);
+    dim3 gridm((unsigned)((c->n + kMixTile - 1) / kMixTile), (unsigned)((W + 31) / 32));
     cudaFuncSetAttribute(tdi_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    tdi_mixed_kernel<K><<<gridm, block, smem, s>>>(c->tdi_tab, W, ldw, c->n, dt, c->orb32,
+    dim3 blockm(32, kMixTile / kMixSpt);
+    tdi_mixed_kernel<K><<<gridm, blockm, smem, s>>>(c->tdi_tab, c->tdi_tiles, W, ldw, c->n,
                                                    (const float*)y, (float*)out, c->data32,
                                                    resid, hlm, hrm);
   }
@@ -358,6 +506,14 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
 }
 
 }  // namespace
+
+cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s) {
+  const int ntiles = (int)((c->n + kTdiTile - 1) / kTdiTile);
+  const int64_t m = (int64_t)ntiles * c->n_dterms;
+  tdi_tiles_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+      c->tdi_tab, c->orb64, c->n, c->cfg.dt, c->cfg.lagrange_order + 1, ntiles, c->tdi_tiles);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_tdi(const lisa_td_ctx* c, int W, int ldw, const void* y, void* out, int resid,
                        cudaStream_t s) {
