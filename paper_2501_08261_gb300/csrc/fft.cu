@@ -33,13 +33,109 @@ __device__ inline C cmulv(C a, C b) {
 
 struct Radices { int r[kMaxRadix]; int nr; };
 
-// one Stockham stage of radix RAD: A (natural sub-blocks of length L) -> B
+// ---- small forward DFTs (W_R = exp(-2 pi i / R)), in registers ------------
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename C>
+__device__ __forceinline__ C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }   // -i a
+
+template <int R, typename C> struct Dft;
+
+template <typename C> struct Dft<2, C> {
+  __device__ __forceinline__ static void run(C* a) {
+    C t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  }
+};
+template <typename C> struct Dft<4, C> {
+  __device__ __forceinline__ static void run(C* a) {
+    C s0 = cadd(a[0], a[2]), s1 = csub(a[0], a[2]);
+    C s2 = cadd(a[1], a[3]), s3 = cmul_mi(csub(a[1], a[3]));
+    a[0] = cadd(s0, s2);
+    a[2] = csub(s0, s2);
+    a[1] = cadd(s1, s3);
+    a[3] = csub(s1, s3);
+  }
+};
+template <typename C> struct Dft<8, C> {
+  __device__ __forceinline__ static void run(C* a) {
+    using T = decltype(a[0].x);
+    const T h = (T)0.70710678118654752440;
+    C e[4] = {a[0], a[2], a[4], a[6]}, o[4] = {a[1], a[3], a[5], a[7]};
+    Dft<4, C>::run(e);
+    Dft<4, C>::run(o);
+    C w1, w3;                                       // W8 o1, W8^3 o3
+    w1.x = h * (o[1].x + o[1].y);  w1.y = h * (o[1].y - o[1].x);
+    C w2 = cmul_mi(o[2]);
+    w3.x = h * (o[3].y - o[3].x);  w3.y = -h * (o[3].x + o[3].y);
+    a[0] = cadd(e[0], o[0]); a[4] = csub(e[0], o[0]);
+    a[1] = cadd(e[1], w1);   a[5] = csub(e[1], w1);
+    a[2] = cadd(e[2], w2);   a[6] = csub(e[2], w2);
+    a[3] = cadd(e[3], w3);   a[7] = csub(e[3], w3);
+  }
+};
+template <typename C> struct Dft<3, C> {
+  __device__ __forceinline__ static void run(C* a) {
+    using T = decltype(a[0].x);
+    const T s3 = (T)0.86602540378443864676;
+    C t = cadd(a[1], a[2]), u = csub(a[1], a[2]);
+    C m; m.x = a[0].x - (T)0.5 * t.x; m.y = a[0].y - (T)0.5 * t.y;
+    a[0] = cadd(a[0], t);
+    // -i sqrt3/2 u
+    C v; v.x = s3 * u.y; v.y = -s3 * u.x;
+    a[1] = cadd(m, v);
+    a[2] = csub(m, v);
+  }
+};
+// R = 5, 7: direct sums with the cosines / sines of 2 pi q / R
+template <int R, typename C> struct DftGeneric {
+  __device__ __forceinline__ static void run(C* a, const double* cs, const double* sn) {
+    using T = decltype(a[0].x);
+    C b[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+      T re = a[0].x, im = a[0].y;
+#pragma unroll
+      for (int q = 1; q < R; ++q) {
+        const int k = (q * s) % R;
+        const T c = (T)cs[k], sv = (T)sn[k];     // W^k = c - i sv
+        re += a[q].x * c + a[q].y * sv;
+        im += a[q].y * c - a[q].x * sv;
+      }
+      b[s].x = re;
+      b[s].y = im;
+    }
+#pragma unroll
+    for (int s = 0; s < R; ++s) a[s] = b[s];
+  }
+};
+__constant__ double c_cos5[5] = {1.0, 0.30901699437494742, -0.80901699437494742,
+                                 -0.80901699437494742, 0.30901699437494742};
+__constant__ double c_sin5[5] = {0.0, 0.95105651629515357, 0.58778525229247313,
+                                 -0.58778525229247313, -0.95105651629515357};
+__constant__ double c_cos7[7] = {1.0, 0.62348980185873353, -0.22252093395631440,
+                                 -0.90096886790241913, -0.90096886790241913,
+                                 -0.22252093395631440, 0.62348980185873353};
+__constant__ double c_sin7[7] = {0.0, 0.78183148246802981, 0.97492791218182361,
+                                 0.43388373911755812, -0.43388373911755812,
+                                 -0.97492791218182361, -0.78183148246802981};
+template <typename C> struct Dft<5, C> {
+  __device__ __forceinline__ static void run(C* a) { DftGeneric<5, C>::run(a, c_cos5, c_sin5); }
+};
+template <typename C> struct Dft<7, C> {
+  __device__ __forceinline__ static void run(C* a) { DftGeneric<7, C>::run(a, c_cos7, c_sin7); }
+};
+
+// one Stockham stage of radix RAD: A (natural sub-blocks of length L) -> B;
+// tw is the m-point table W_m^j in shared memory
 template <int RAD, typename C>
 __device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, int P,
                       const C* __restrict__ tw, int tid, int nth) {
   const int nb = m / RAD;
   const int stride = m / (L * RAD);
-  const int rstep = m / RAD;
   for (int item = tid; item < nb * P; item += nth) {
     const int p = item % P, j = item / P;
     const int k = j % L;
@@ -49,18 +145,10 @@ __device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, 
       a[q] = A[(j + q * nb) * P + p];
       if (q > 0 && k > 0) a[q] = cmulv(a[q], tw[k * q * stride]);
     }
+    Dft<RAD, C>::run(a);
     const int base = (j - k) * RAD + k;
 #pragma unroll
-    for (int s = 0; s < RAD; ++s) {
-      C b = a[0];
-#pragma unroll
-      for (int q = 1; q < RAD; ++q) {
-        C t = cmulv(a[q], tw[((q * s) % RAD) * rstep]);
-        b.x += t.x;
-        b.y += t.y;
-      }
-      B[(base + s * L) * P + p] = b;
-    }
+    for (int s = 0; s < RAD; ++s) B[(base + s * L) * P + p] = a[s];
   }
 }
 
@@ -91,7 +179,7 @@ __device__ C* transform(C* buf0, C* buf1, int m, int P, const Radices& rd,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) pass1_kernel(const R* __restrict__ x,
+__global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
                                                     typename CT<R>::T* __restrict__ fy, int64_t n,
                                                     int n1, int n2, int Pt, int Pb, Radices rd,
                                                     const typename CT<R>::T* __restrict__ tw1,
@@ -101,6 +189,8 @@ __global__ void __launch_bounds__(256) pass1_kernel(const R* __restrict__ x,
   extern __shared__ unsigned char smem_raw[];
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + (size_t)n1 * Pb;
+  C* tws = b1 + (size_t)n1 * Pb;                   // W_n1^j, j < n1
+  for (int j = threadIdx.x; j < n1; j += blockDim.x) tws[j] = tw1[j];
   const int b = blockIdx.x;
   const int pb0 = blockIdx.y * Pb;
   const int c = chans[blockIdx.z];
@@ -111,7 +201,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(const R* __restrict__ x,
     b0[item] = xc[((int64_t)n2 * a + b) * Pt + pb0 + p];
   }
   __syncthreads();
-  C* res = transform(b0, b1, n1, Pb, rd, tw1);
+  C* res = transform(b0, b1, n1, Pb, rd, (const C*)tws);
   C* out = fy + (int64_t)c * n * Pt;
   for (int item = threadIdx.x; item < n1 * Pb; item += blockDim.x) {
     const int k1 = item / Pb, p = item % Pb;
@@ -121,7 +211,7 @@ __global__ void __launch_bounds__(256) pass1_kernel(const R* __restrict__ x,
 }
 
 template <typename R>
-__global__ void __launch_bounds__(256) pass2_kernel(const typename CT<R>::T* __restrict__ fy,
+__global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __restrict__ fy,
                                                     double* __restrict__ partial, int64_t n,
                                                     int n1, int n2, int Pt, int Pb, Radices rd,
                                                     const typename CT<R>::T* __restrict__ tw2,
@@ -133,7 +223,9 @@ __global__ void __launch_bounds__(256) pass2_kernel(const typename CT<R>::T* __r
   C* a1 = a0 + (size_t)n2 * Pb;
   C* c0 = a1 + (size_t)n2 * Pb;
   C* c1 = c0 + (size_t)n2 * Pb;
-  __shared__ double red[256];
+  C* tws = c1 + (size_t)n2 * Pb;                   // W_n2^j, j < n2
+  for (int j = threadIdx.x; j < n2; j += blockDim.x) tws[j] = tw2[j];
+  __shared__ double red[512];
   const int rp = blockIdx.x;
   const int pb0 = blockIdx.y * Pb;
   const int c = chans[blockIdx.z];
@@ -146,11 +238,12 @@ __global__ void __launch_bounds__(256) pass2_kernel(const typename CT<R>::T* __r
     if (!single) c0[item] = in[((int64_t)rB * n2 + j) * Pt + pb0 + p];
   }
   __syncthreads();
-  C* XA = transform(a0, a1, n2, Pb, rd, tw2);
-  C* XB = single ? XA : transform(c0, c1, n2, Pb, rd, tw2);
+  C* XA = transform(a0, a1, n2, Pb, rd, (const C*)tws);
+  C* XB = single ? XA : transform(c0, c1, n2, Pb, rd, (const C*)tws);
   const int64_t nb = n / 2 + 1;
   const double* wv = psdw + (c == 2 ? nb : 0);
-  double accx = 0.0, accy = 0.0;           // walker 2p, 2p+1 (p fixed per thread)
+  double accx = 0.0, accy = 0.0;     // walker 2p, 2p+1 (p fixed per thread); FP64: the
+                                     // weights 4 df dt^2 / S reach ~1e47, beyond FP32
   const int nrow = single ? 1 : 2;
   for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
     const int k2 = item / Pb, p = item % Pb;
@@ -165,8 +258,8 @@ __global__ void __launch_bounds__(256) pass2_kernel(const typename CT<R>::T* __r
       const int km = (single && row == 0) ? (n2 - k2) % n2 : n2 - 1 - k2;
       C z = X[k2 * Pb + p];
       C zm = Xm[km * Pb + p];
-      double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
-      double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
+      const double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
+      const double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
       accx += wk * (xr * xr + xi * xi);
       accy += wk * (yr * yr + yi * yi);
     }
@@ -202,8 +295,9 @@ __global__ void reduce_kernel(const double* __restrict__ partial, int nrp, int W
 
 int pick_pb(int m, int nbuf, size_t csize, int Pt) {
   int pb = 16;
-  while (pb > 1 && ((size_t)nbuf * m * pb * csize > 200 * 1024 || Pt % pb != 0)) pb /= 2;
-  return ((size_t)nbuf * m * pb * csize > 200 * 1024) ? 0 : pb;
+  auto bytes = [&](int q) { return ((size_t)nbuf * q + 1) * m * csize; };
+  while (pb > 1 && (bytes(pb) > 200 * 1024 || Pt % pb != 0)) pb /= 2;
+  return bytes(pb) > 200 * 1024 ? 0 : pb;
 }
 
 void radices_of(int m, Radices* rd) {
@@ -232,18 +326,18 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
   int pb1 = pick_pb(p.n1, 2, sizeof(C), Pt);
   int pb2 = pick_pb(p.n2, 4, sizeof(C), Pt);
   if (pb1 == 0 || pb2 == 0) return cudaErrorInvalidValue;
-  size_t sm1 = (size_t)2 * p.n1 * pb1 * sizeof(C);
-  size_t sm2 = (size_t)4 * p.n2 * pb2 * sizeof(C);
+  size_t sm1 = ((size_t)2 * pb1 + 1) * p.n1 * sizeof(C);
+  size_t sm2 = ((size_t)4 * pb2 + 1) * p.n2 * sizeof(C);
   cudaFuncSetAttribute(pass1_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
   cudaFuncSetAttribute(pass2_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
   const int* chans = c->chan_list;
   if (pass == 1) {
     dim3 g1((unsigned)p.n2, (unsigned)(Pt / pb1), (unsigned)nch);
-    pass1_kernel<R><<<g1, 256, sm1, s>>>((const R*)r, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
+    pass1_kernel<R><<<g1, 512, sm1, s>>>((const R*)r, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
                                          (const C*)p.tw1, (const C*)p.tw_n, chans);
   } else {
     dim3 g2((unsigned)(p.n1 / 2 + 1), (unsigned)(Pt / pb2), (unsigned)nch);
-    pass2_kernel<R><<<g2, 256, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
+    pass2_kernel<R><<<g2, 512, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
                                          pb2, r2, (const C*)p.tw2, c->psdw, chans);
   }
   return cudaGetLastError();

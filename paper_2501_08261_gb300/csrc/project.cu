@@ -121,19 +121,24 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
 // spacecraft offsets k.rho (FP32 table relative to g) enter only as small
 // FP32 numbers next to exact integers.
 template <int K>
-__global__ void __launch_bounds__(128) project_mixed_kernel(
+__global__ void __launch_bounds__(256) project_mixed_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
     int tile, int halo, int nL, float rL) {
-  extern __shared__ float2 winf[];      // [(tile + 2 halo)][kPW]
+  // shared memory: h+ and hx planes [rows][32] (walker = bank: conflict-free
+  // whatever each walker's stencil row), then the tile's orbit records
+  extern __shared__ float smf[];
+  const int rows = tile + 2 * halo;
+  float* hps = smf;
+  float* hcs = smf + rows * 32;
+  OrbitRec32* ors = reinterpret_cast<OrbitRec32*>(smf + 2 * rows * 32);
   __shared__ int shift_s[32];
   __shared__ float fra_s[32], p1_s[32], sa_s[32];
   __shared__ float cinv_s[K];
   const int lane = threadIdx.x, warp = threadIdx.y, nw = blockDim.y;
-  const int tid = warp * 32 + lane;
+  const int tid = warp * 32 + lane, nth = 32 * nw;
   const int64_t i0 = (int64_t)blockIdx.x * tile;
   const int w = blockIdx.y * 32 + lane;
-  const int rows = tile + 2 * halo;
   if (tid < K) cinv_s[tid] = lagrange_denom_inv<float, K>(tid);
   if (warp == 0) {
     const WalkerRec& R = walkers[w];
@@ -147,13 +152,22 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(
     p1_s[lane] = (float)(kAUSec * (-R.k[0] * sa + R.k[1] * ca));
     sa_s[lane] = (float)S;
   }
+  {  // orbit records of the tile (coalesced words)
+    const int64_t nrec = (i0 + tile <= n) ? tile : (n - i0);
+    const int words = (int)nrec * (int)(sizeof(OrbitRec32) / sizeof(float));
+    const float* src = reinterpret_cast<const float*>(orb + i0);
+    float* dst = reinterpret_cast<float*>(ors);
+    for (int q = tid; q < words; q += nth) dst[q] = src[q];
+  }
   __syncthreads();
-  for (int ww = warp; ww < 32; ww += nw) {
-    const int64_t a0 = i0 - shift_s[ww] - halo;
-    const float2* hw = h + (int64_t)(blockIdx.y * 32 + ww) * n;
-    for (int r = lane; r < rows; r += 32) {
-      int64_t g = a0 + r;
-      winf[r * kPW + ww] = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
+  {  // h windows: lane = walker, each warp a strided set of rows
+    const int64_t a0w = i0 - shift_s[lane] - halo;
+    const float2* hw = h + (int64_t)w * n;
+    for (int r = warp; r < rows; r += nw) {
+      int64_t g = a0w + r;
+      float2 v = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
+      hps[r * 32 + lane] = v.x;
+      hcs[r * 32 + lane] = v.y;
     }
   }
   __syncthreads();
@@ -180,9 +194,8 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(
     if (loc >= 0 && loc + K <= rows) {
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        float2 v = winf[(loc + j) * kPW + lane];
-        sp = fmaf(wts[j], v.x, sp);
-        sc = fmaf(wts[j], v.y, sc);
+        sp = fmaf(wts[j], hps[(loc + j) * 32 + lane], sp);
+        sc = fmaf(wts[j], hcs[(loc + j) * 32 + lane], sc);
       }
     } else {
       for (int j = 0; j < K; ++j) {
@@ -201,7 +214,7 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(
   for (int s = warp; s < tile; s += nw) {
     const int64_t i = i0 + s;
     if (i >= n) break;
-    const OrbitRec32& O = orb[i];
+    const OrbitRec32& O = ors[s];
     const float d = odt * (float)s;
     const float dS = d * p1 - 0.5f * d * d * sa;     // k.g(t) - k.g(t_a)
     const float base_f = -fra - dS * idt;
@@ -215,13 +228,13 @@ __global__ void __launch_bounds__(128) project_mixed_kernel(
     for (int j = 0; j < kNLink; ++j) {
       const int rq = link_receiver(j);
       float ks = k0 * O.rs[j][0] + k1 * O.rs[j][1] + k2 * O.rs[j][2];
-      float hps, hcs;
-      interp(s + halo - nL, base_f - rL - (O.L[j] + ks) * idt, hps, hcs);
+      float hps_, hcs_;
+      interp(s + halo - nL, base_f - rL - (O.L[j] + ks) * idt, hps_, hcs_);
       float nx = O.n[j][0], ny = O.n[j][1], nz = O.n[j][2];
       float un = u0 * nx + u1 * ny + u2 * nz;
       float vn = v0 * nx + v1 * ny + v2 * nz;
       float kn = k0 * nx + k1 * ny + k2 * nz;
-      float val = ((un * un - vn * vn) * (hps - hpr[rq]) + 2.0f * un * vn * (hcs - hcr[rq])) /
+      float val = ((un * un - vn * vn) * (hps_ - hpr[rq]) + 2.0f * un * vn * (hcs_ - hcr[rq])) /
                   (2.0f * (1.0f - kn));
       if (w < W) y[((int64_t)j * n + i) * ldw + w] = val;
     }
@@ -246,13 +259,15 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
                                                      c->orb64, (const double2*)h, (double*)y,
                                                      tile, halo);
   } else {
-    size_t smem = (size_t)(tile + 2 * halo) * kPW * sizeof(float2);
+    size_t smem = (size_t)2 * (tile + 2 * halo) * 32 * sizeof(float) +
+                  (size_t)tile * sizeof(OrbitRec32);
     double q = kArmSec / dt;
     int nL = (int)floor(q);
     float rL = (float)(q - nL);
     cudaFuncSetAttribute(project_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    project_mixed_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
+    dim3 blockm(32, 8);
+    project_mixed_kernel<K><<<grid, blockm, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                       c->orb32, (const float2*)h, (float*)y,
                                                       tile, halo, nL, rL);
   }

@@ -246,9 +246,17 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
       if (m >= 0 && o > m) c += w[k];
       if (m < 0 && o <= m) c -= w[k];
     }
-    const float cf = (float)c;
-    R.C[mi] = cf;
-    mom += (double)cf - c;
+    if (m == 0) {
+      // the linear-interpolation part eps_a dy_c goes to the compensated main
+      // accumulator in the kernel; the table keeps the remainder
+      const float cf = (float)(c - (double)R.eps_a);
+      R.C[mi] = cf;
+      mom += ((double)R.eps_a + (double)cf) - c;
+    } else {
+      const float cf = (float)c;
+      R.C[mi] = cf;
+      mom += (double)cf - c;
+    }
   }
   R.m1 = (float)mom;
   R.pad[0] = R.pad[1] = 0;
@@ -257,49 +265,78 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
 
 constexpr int kMixTile = kTdiTile;
 constexpr int kMixSpt = 8;                  // samples per thread (8 warps x 8 = 64)
-constexpr int kPW2 = 33;                 // padded walkers per row
+constexpr int kMixWarps = kMixTile / kMixSpt;
+constexpr int kPW2 = 33;                    // padded walker pairs per row
 
-__device__ __forceinline__ void add_scaled(float (&dst)[kMixSpt], const float (&src)[kMixSpt],
-                                           float sg) {
+struct f2 { float x, y; };                  // two walkers of one lane
+__device__ __forceinline__ f2 ld2(const float2* p) { float2 v = *p; return {v.x, v.y}; }
+
+// compensated (Knuth two-sum) accumulation of the |y|-sized centre samples:
+// hi + lo keeps their sum exact to ~2^-48, so that the TDI cancellation in X,
+// Y, Z (and further in T) is not limited by FP32 rounding of these sums; the
+// lo parts go to the small accumulator
+__device__ __forceinline__ void acc2(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (v - bb);
+  hi = s;
+}
+
+template <int SPT>
+__device__ __forceinline__ void add_rows(f2 (&hi)[SPT], f2 (&lo)[SPT], const float2* __restrict__ yw,
+                                         int row0, float sg, int lane) {
 #pragma unroll
-  for (int r = 0; r < kMixSpt; ++r) {
-    dst[r] = fmaf(sg, src[r], dst[r]);
+  for (int r = 0; r < SPT; ++r) {
+    const f2 v = ld2(&yw[(row0 + r) * kPW2 + lane]);
+    acc2(hi[r].x, lo[r].x, sg * v.x);
+    acc2(hi[r].y, lo[r].y, sg * v.y);
   }
 }
 
-// small[r] += sg * (sum_{m'} C[m'] dy[b0 + r + m'] + (j (a1 + j a2) - m1) dy[b0 + r + H])
-// (the centre sample y_c is accumulated separately by the caller)
+// small[r] += sum_{m'} c[m'] dy[b0 + r + m'] + dr_r dy[b0 + r + H], c and dr carrying the
+// sign; the linear-interpolation part sg eps_a dy[b0 + r + H] is added to the main
+// accumulator exactly (FMA two-product, two-sum), since its rounding in the small
+// accumulator is noise of size ulp(|dy|) that TDI 2's T channel no longer suppresses
 template <int K, int SPT>
-__device__ __forceinline__ void apply_tile_term(float (&acc)[SPT], const float* __restrict__ dyw,
-                                                const TdiTileTerm* __restrict__ P, float sg,
-                                                int s0, int b0, int lane) {
+__device__ __forceinline__ void apply_tile_term(f2 (&main)[SPT], f2 (&acc)[SPT],
+                                                const float2* __restrict__ dyw,
+                                                const TdiTileTerm& P, float sg, int s0, int b0,
+                                                int lane) {
   constexpr int H = (K - 2) / 2;
   constexpr int NT = K - 1;                       // taps on the differences
   float c[NT];
 #pragma unroll
-  for (int k = 0; k < NT; ++k) c[k] = sg * P->C[k];
-  const float m1 = P->m1, a1 = P->a1, a2 = P->a2;
-  float win[SPT];
+  for (int k = 0; k < NT; ++k) c[k] = sg * P.C[k];
+  const float m1 = P.m1, a1 = P.a1, a2 = P.a2, se = sg * P.eps_a;
+  f2 win[SPT];
 #pragma unroll
-  for (int r = 0; r < SPT; ++r) win[r] = dyw[(b0 + r) * kPW2 + lane];
+  for (int r = 0; r < SPT; ++r) win[r] = ld2(&dyw[(b0 + r) * kPW2 + lane]);
 #pragma unroll
   for (int m = 0; m < NT; ++m) {
 #pragma unroll
     for (int r = 0; r < SPT; ++r) {
-      acc[r] = fmaf(c[m], win[r], acc[r]);
+      acc[r].x = fmaf(c[m], win[r].x, acc[r].x);
+      acc[r].y = fmaf(c[m], win[r].y, acc[r].y);
     }
     if (m == H) {                                 // win[r] = dy at the centre
 #pragma unroll
       for (int r = 0; r < SPT; ++r) {
         const float jj = (float)(s0 + r);
         const float dr = sg * (jj * fmaf(jj, a2, a1) - m1);
-        acc[r] = fmaf(dr, win[r], acc[r]);
+        acc[r].x = fmaf(dr, win[r].x, acc[r].x);
+        acc[r].y = fmaf(dr, win[r].y, acc[r].y);
+        const float px = se * win[r].x, py = se * win[r].y;
+        const float ex = fmaf(se, win[r].x, -px), ey = fmaf(se, win[r].y, -py);
+        acc2(main[r].x, acc[r].x, px);
+        acc2(main[r].y, acc[r].y, py);
+        acc[r].x += ex;
+        acc[r].y += ey;
       }
     }
     if (m + 1 < NT) {
 #pragma unroll
       for (int r = 0; r < SPT - 1; ++r) win[r] = win[r + 1];
-      win[SPT - 1] = dyw[(b0 + SPT + m) * kPW2 + lane];
+      win[SPT - 1] = ld2(&dyw[(b0 + SPT + m) * kPW2 + lane]);
     }
   }
 }
@@ -307,17 +344,16 @@ __device__ __forceinline__ void apply_tile_term(float (&acc)[SPT], const float* 
 // tiles whose fraction wraps inside the tile (rare): per-sample FP32 weights,
 // still as y_c' + sum w_k (y_k - y_c') so that their DC error meets only differences
 template <int K>
-__device__ __noinline__ void split_one(const float* __restrict__ yw,
-                                       const TdiTileTerm* __restrict__ P, int s, int hl,
-                                       int rows, int lane, float& yc_out, float& small_out) {
+__device__ __noinline__ float4 split_one(const float2* __restrict__ yw, const TdiTileTerm* P,
+                                         int s, int hl, int rows, int lane) {
   const int H = (K - 2) / 2;
   const float jj = (float)s;
   float e = P->eps_a + jj * fmaf(jj, P->a2, P->a1);
   float fl = floorf(e);
   float eps = e - fl;
   const int c = s + hl + P->bo + (int)fl;
-  const float yc = (c >= 0 && c < rows) ? yw[c * kPW2 + lane] : 0.0f;
-  float ax = 0.0f;
+  const float2 yc = (c >= 0 && c < rows) ? yw[c * kPW2 + lane] : make_float2(0.0f, 0.0f);
+  float ax = 0.0f, ay = 0.0f;
   for (int k = 0; k < K; ++k) {
     float num = 1.0f, den = 1.0f;
     for (int m = 0; m < K; ++m) {
@@ -327,80 +363,62 @@ __device__ __noinline__ void split_one(const float* __restrict__ yw,
     }
     const float wk = num / den;
     const int row = c + k - H;
-    float v = (row >= 0 && row < rows) ? yw[row * kPW2 + lane] : 0.0f;
-    ax = fmaf(wk, v - yc, ax);
+    float2 v = (row >= 0 && row < rows) ? yw[row * kPW2 + lane] : make_float2(0.0f, 0.0f);
+    ax = fmaf(wk, v.x - yc.x, ax);
+    ay = fmaf(wk, v.y - yc.y, ay);
   }
-  yc_out = yc;
-  small_out = ax;
+  return make_float4(yc.x, yc.y, ax, ay);
 }
 
-// compensated (Knuth two-sum) accumulation of the |y|-sized centre samples:
-// hi + lo keeps their sum exact to ~2^-48, so that the TDI cancellation in
-// X, Y, Z (and further in T) is not limited by FP32 rounding of these sums
-template <int SPT>
-__device__ __forceinline__ void add_rows(float (&hi)[SPT], float (&lo)[SPT],
-                                         const float* __restrict__ yw, int row0, float sg,
-                                         int lane) {
-#pragma unroll
-  for (int r = 0; r < SPT; ++r) {
-    const float v = sg * yw[(row0 + r) * kPW2 + lane];
-    const float s = hi[r] + v;
-    const float bb = s - hi[r];
-    lo[r] += (hi[r] - (s - bb)) + (v - bb);
-    hi[r] = s;
-  }
-}
-template <int SPT>
-__device__ __forceinline__ void add_vals(float (&hi)[SPT], float (&lo)[SPT], const float (&src)[SPT],
-                                         float sg) {
-#pragma unroll
-  for (int r = 0; r < SPT; ++r) {
-    const float v = sg * src[r];
-    const float s = hi[r] + v;
-    const float bb = s - hi[r];
-    lo[r] += (hi[r] - (s - bb)) + (v - bb);
-    hi[r] = s;
-  }
-}
-
-// Accumulators: `main` holds the |y|-sized centre samples of every term, `small`
-// the difference FIRs and corrections; X = main + small only at the end, where
-// the TDI cancellation has made X small.
+// One CTA = 64 walkers (two per lane) x 64 output samples (8 warps x 8).
+// Accumulators: `m*` hold the |y|-sized centre samples of every term
+// (compensated), `s*` the difference FIRs, corrections and compensation terms;
+// A, E, T are formed from the m parts error-free before the s parts are added.
 template <int K>
-__global__ void __launch_bounds__(32 * (kMixTile / kMixSpt), 2) tdi_mixed_kernel(
+__global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
     const TdiTable* __restrict__ tab, const TdiTileTerm* __restrict__ tiles, int W, int ldw,
     int64_t n, const float* __restrict__ y, float* __restrict__ out,
     const float* __restrict__ data, int resid, int hl, int hr) {
   constexpr int SPT = kMixSpt;
-  constexpr int NWP = kMixTile / kMixSpt;
-  extern __shared__ float smem2[];
+  extern __shared__ float2 smem2[];
   const int rows = kMixTile + hl + hr;
-  float* yw = smem2;                              // [rows][kPW2]
-  float* dyw = smem2 + rows * kPW2;               // [rows][kPW2], dy_r = y_{r+1} - y_r
+  float2* yw = smem2;                              // [rows][kPW2]
+  float2* dyw = smem2 + rows * kPW2;               // dy_r = y_{r+1} - y_r
+  __shared__ TdiTileTerm tts[42];
   const int lane = threadIdx.x, warp = threadIdx.y;
+  const int tid = warp * 32 + lane;
   const int64_t i0 = (int64_t)blockIdx.x * kMixTile;
-  const int w = blockIdx.y * 32 + lane;
+  const int wa = blockIdx.y * 64 + 2 * lane;       // walkers wa, wa + 1
   const int s0 = warp * SPT;
   const int nd = tab->n_dterms;
-  const TdiTileTerm* tt = tiles + (int64_t)blockIdx.x * nd;
-  float mx[SPT], my[SPT], mz[SPT], sx[SPT], sy[SPT], sz[SPT];   // main (hi) and small
+  {
+    const int* src = reinterpret_cast<const int*>(tiles + (int64_t)blockIdx.x * nd);
+    int* dst = reinterpret_cast<int*>(tts);
+    const int words = nd * (int)(sizeof(TdiTileTerm) / sizeof(int));
+    for (int q = tid; q < words; q += 32 * kMixWarps) dst[q] = src[q];
+  }
+  f2 mx[SPT], my[SPT], mz[SPT], sx[SPT], sy[SPT], sz[SPT];
 #pragma unroll
   for (int r = 0; r < SPT; ++r)
-    mx[r] = my[r] = mz[r] = sx[r] = sy[r] = sz[r] = 0.0f;
+    mx[r] = my[r] = mz[r] = sx[r] = sy[r] = sz[r] = f2{0.0f, 0.0f};
 
   for (int j = 0; j < kNLink; ++j) {
     __syncthreads();
-    for (int r = warp; r < rows; r += NWP) {
+    for (int r = warp; r < rows; r += kMixWarps) {
       int64_t g = i0 - hl + r;
-      float v = 0.0f;
-      if (g >= 0 && g < n && w < W) v = y[((int64_t)j * n + g) * ldw + w];
+      float2 v = make_float2(0.0f, 0.0f);
+      if (g >= 0 && g < n) {
+        const float* src = y + ((int64_t)j * n + g) * ldw;
+        if (wa < W) v.x = src[wa];
+        if (wa + 1 < W) v.y = src[wa + 1];
+      }
       yw[r * kPW2 + lane] = v;
     }
     __syncthreads();
-    for (int r = warp; r < rows; r += NWP) {
-      float a = yw[r * kPW2 + lane];
-      float b = r + 1 < rows ? yw[(r + 1) * kPW2 + lane] : a;
-      dyw[r * kPW2 + lane] = b - a;
+    for (int r = warp; r < rows; r += kMixWarps) {
+      float2 a = yw[r * kPW2 + lane];
+      float2 b = r + 1 < rows ? yw[(r + 1) * kPW2 + lane] : a;
+      dyw[r * kPW2 + lane] = make_float2(b.x - a.x, b.y - a.y);
     }
     __syncthreads();
     const int nt = tab->nterm[j];
@@ -413,33 +431,34 @@ __global__ void __launch_bounds__(32 * (kMixTile / kMixSpt), 2) tdi_mixed_kernel
         else add_rows<SPT>(mz, sz, yw, s0 + hl, sg, lane);
         continue;
       }
-      const TdiTileTerm* P = tt + tab->dterm[j][q];
-      if (!P->split) {
-        const int c0 = s0 + hl + P->bo;            // centre row of sample s0
+      const TdiTileTerm& P = tts[tab->dterm[j][q]];
+      if (!P.split) {
+        const int c0 = s0 + hl + P.bo;             // centre row of sample s0
         const int b0 = c0 - (K - 2) / 2;
         if (T.chan == 0) {
           add_rows<SPT>(mx, sx, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(sx, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(mx, sx, dyw, P, sg, s0, b0, lane);
         } else if (T.chan == 1) {
           add_rows<SPT>(my, sy, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(sy, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(my, sy, dyw, P, sg, s0, b0, lane);
         } else {
           add_rows<SPT>(mz, sz, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(sz, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(mz, sz, dyw, P, sg, s0, b0, lane);
         }
       } else {
-        float ycv[SPT], smv[SPT];
 #pragma unroll
-        for (int r = 0; r < SPT; ++r) split_one<K>(yw, P, s0 + r, hl, rows, lane, ycv[r], smv[r]);
-        if (T.chan == 0) {
-          add_vals<SPT>(mx, sx, ycv, sg);
-          add_scaled(sx, smv, sg);
-        } else if (T.chan == 1) {
-          add_vals<SPT>(my, sy, ycv, sg);
-          add_scaled(sy, smv, sg);
-        } else {
-          add_vals<SPT>(mz, sz, ycv, sg);
-          add_scaled(sz, smv, sg);
+        for (int r = 0; r < SPT; ++r) {
+          const float4 v = split_one<K>(yw, &P, s0 + r, hl, rows, lane);
+          if (T.chan == 0) {
+            acc2(mx[r].x, sx[r].x, sg * v.x); acc2(mx[r].y, sx[r].y, sg * v.y);
+            sx[r].x = fmaf(sg, v.z, sx[r].x); sx[r].y = fmaf(sg, v.w, sx[r].y);
+          } else if (T.chan == 1) {
+            acc2(my[r].x, sy[r].x, sg * v.x); acc2(my[r].y, sy[r].y, sg * v.y);
+            sy[r].x = fmaf(sg, v.z, sy[r].x); sy[r].y = fmaf(sg, v.w, sy[r].y);
+          } else {
+            acc2(mz[r].x, sz[r].x, sg * v.x); acc2(mz[r].y, sz[r].y, sg * v.y);
+            sz[r].x = fmaf(sg, v.z, sz[r].x); sz[r].y = fmaf(sg, v.w, sz[r].y);
+          }
         }
       }
     }
@@ -455,20 +474,25 @@ __global__ void __launch_bounds__(32 * (kMixTile / kMixSpt), 2) tdi_mixed_kernel
       dE = data[n + i];
       dT = data[2 * n + i];
     }
-    if (w >= W) continue;
-    // A, E, T from the main (hi) parts combined error-free first, the small
-    // parts after: T = (X + Y + Z)/sqrt3 cancels the signal further still
-    df32 zx = two_sum(mz[r], -mx[r]);
-    df32 xy = two_sum(mx[r], -2.0f * my[r]);
-    df32 xyz = two_sum(xy.hi, mz[r]);
-    df32 xy3 = two_sum(mx[r], my[r]);
-    df32 t3 = two_sum(xy3.hi, mz[r]);
-    const float A = zx.hi + (zx.lo + (sz[r] - sx[r]));
-    const float E = xyz.hi + ((xy.lo + xyz.lo) + (sx[r] - 2.0f * sy[r] + sz[r]));
-    const float Tt = t3.hi + ((xy3.lo + t3.lo) + (sx[r] + sy[r] + sz[r]));
-    out[(0 * n + i) * ldw + w] = A * r2 - dA;
-    out[(1 * n + i) * ldw + w] = E * r6 - dE;
-    out[(2 * n + i) * ldw + w] = Tt * r3 - dT;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int w = wa + e;
+      if (w >= W) continue;
+      const float Mx = e ? mx[r].y : mx[r].x, My = e ? my[r].y : my[r].x, Mz = e ? mz[r].y : mz[r].x;
+      const float Sx = e ? sx[r].y : sx[r].x, Sy = e ? sy[r].y : sy[r].x, Sz = e ? sz[r].y : sz[r].x;
+      // A, E, T from the main parts combined error-free first, the small parts after
+      df32 zx = two_sum(Mz, -Mx);
+      df32 xy = two_sum(Mx, -2.0f * My);
+      df32 xyz = two_sum(xy.hi, Mz);
+      df32 xy3 = two_sum(Mx, My);
+      df32 t3 = two_sum(xy3.hi, Mz);
+      const float A = zx.hi + (zx.lo + (Sz - Sx));
+      const float E = xyz.hi + ((xy.lo + xyz.lo) + (Sx - 2.0f * Sy + Sz));
+      const float Tt = t3.hi + ((xy3.lo + t3.lo) + (Sx + Sy + Sz));
+      out[(0 * n + i) * ldw + w] = A * r2 - dA;
+      out[(1 * n + i) * ldw + w] = E * r6 - dE;
+      out[(2 * n + i) * ldw + w] = Tt * r3 - dT;
+    }
   }
 }
 
@@ -493,8 +517,8 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
   } else {
     int hlm = (int)ceil(nd * 1.1 * kArmSec / dt) + K / 2 + 3;
     int hrm = K / 2 + 2;
-    size_t smem = (size_t)2 * (kMixTile + hlm + hrm) * kPW2 * sizeof(float);
-    dim3 gridm((unsigned)((c->n + kMixTile - 1) / kMixTile), (unsigned)((W + 31) / 32));
+    size_t smem = (size_t)2 * (kMixTile + hlm + hrm) * kPW2 * sizeof(float2);
+    dim3 gridm((unsigned)((c->n + kMixTile - 1) / kMixTile), (unsigned)((W + 63) / 64));
     cudaFuncSetAttribute(tdi_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     dim3 blockm(32, kMixTile / kMixSpt);
