@@ -114,6 +114,32 @@ int lisa_td_loglike_batch(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
 int lisa_td_profile(lisa_td_ctx* ctx, int32_t enable);
 int lisa_td_profile_read(lisa_td_ctx* ctx, double* stage_ms, int64_t* calls);
 
+/* No-allocation variant of the DFT + PSD-weighted norm stages.  The paper has
+ * no counterpart: this is a service for callers that must not allocate device
+ * memory -- processes whose device memory a framework's caching pool already
+ * holds (a cudaMalloc of the library's own can fail although the pool has free
+ * blocks), or sampler loops that cannot take the device-wide synchronisation
+ * that cudaFree implies.  It needs no context and calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   logl_dev[w] = -1/2 sum_{c in cfg->channel_mask} (r_c | r_c),   w < W,
+ * for residual series r = h - d the caller supplies: r_dev is [3][n][W]
+ * (channel A, E, T, then sample, walker fastest), double when
+ * cfg->precision == 0 and float when 1, 16- (double) or 8-byte (float)
+ * aligned.  Fields of cfg used: dt, n, f_lo, f_hi, tdi_gen (PSD), channel_mask,
+ * precision; the others are ignored.  W must be even (series are transformed
+ * in pairs; pad with a zero series).  With r = AET(theta) - d it returns what
+ * lisa_td_loglike_batch returns for theta.
+ * Limit: all scratch lives in one static 32 MiB device array, held on every
+ * GPU that loads the library until the process exits; about 3 n W x 8 (FP64)
+ * or x 4 (mixed) bytes are needed, and larger (n, W) fail with LISA_TD_ERANGE
+ * (n = 17280 allows W <= 78 in FP64, W <= 158 mixed).  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the array: calls that can
+ * overlap on the GPU (different streams, or several host threads) race and
+ * give wrong results; order them on one stream. */
+int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_dev, int32_t W,
+                                     double* logl_dev, void* stream);
+
 void lisa_td_destroy(lisa_td_ctx* ctx);
 const char* lisa_td_last_error(void);
 

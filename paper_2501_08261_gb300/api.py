@@ -14,7 +14,7 @@ LISA_TD_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
-           "lisa_td_destroy", "lisa_td_last_error")
+           "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc")
 NSTAGE = 7
 STAGES = ("prep", "waveform", "project", "tdi", "fft_pass1", "fft_pass2_norm", "reduce")
 
@@ -46,6 +46,7 @@ def load_library(path=None):
         "lisa_td_profile": ([P, I32], ctypes.c_int),
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
+        "lisa_td_residual_loglike_noalloc": ([ctypes.POINTER(Config), P, I32, P, P], ctypes.c_int),
         "lisa_td_destroy": ([P], None),
         "lisa_td_last_error": ([], ctypes.c_char_p),
     }
@@ -135,6 +136,15 @@ def lisa_td_profile_read(ctx):
     calls = ctypes.c_int64()
     _check(lib().lisa_td_profile_read(ctx, arr, ctypes.byref(calls)), "lisa_td_profile_read")
     return dict(zip(STAGES, list(arr))), calls.value
+
+
+def lisa_td_residual_loglike_noalloc(cfg, r, W, logl, stream=None):
+    """-1/2 sum_c (r_c | r_c) per walker from caller-supplied residual series
+    r [3][n][W] (W even) with scratch in the library's static device array:
+    for callers that must not allocate device memory (see include/lisa_td.h)."""
+    _check(lib().lisa_td_residual_loglike_noalloc(ctypes.byref(cfg), _ptr(r), int(W), _ptr(logl),
+                                                  _stream(stream)),
+           "lisa_td_residual_loglike_noalloc")
 
 
 def lisa_td_destroy(ctx):

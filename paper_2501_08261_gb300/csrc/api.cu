@@ -76,6 +76,16 @@ inline int pad32(int w) { return (w + 31) / 32 * 32; }
 
 }  // namespace
 
+namespace lisa {
+int report_error(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+}  // namespace lisa
+
 extern "C" {
 
 const char* lisa_td_last_error(void) { return g_err; }

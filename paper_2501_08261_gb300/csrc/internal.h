@@ -77,6 +77,8 @@ cudaError_t launch_fft_pass2(const lisa_td_ctx* c, int Wpad, cudaStream_t s);
 cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl,
                           int32_t* status, cudaStream_t s);
 int plan_fft(int64_t n, FftPlan* p);
+// api.cu: set the thread's lisa_td_last_error() text, return `code`
+int report_error(int code, const char* fmt, ...);
 TdiTable build_tdi_table(int gen);
 cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s);
 

@@ -1,0 +1,72 @@
+"""lisa_td_residual_loglike_noalloc: the DFT + PSD-weighted norm for callers
+that must not allocate device memory (their memory sits in a framework's
+caching pool, or their loop cannot take the synchronisation cudaFree implies).
+Its scratch is a fixed static device array, so it must give what
+lisa_td_loglike_batch gives for the same walkers, call after call, and refuse
+sizes the array cannot hold.  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2501_08261_gb300 import api, workloads
+
+from helpers import gpu_kwargs
+
+torch = pytest.importorskip("torch")
+
+
+def test_rejects_sizes_beyond_the_static_scratch():
+    # the size and shape checks return before any CUDA call, so no GPU is needed
+    lib = api.load_library(api._build.build())
+    fake = ctypes.c_void_p(1 << 20)                   # never dereferenced
+    big = api.make_config(dt=5.0, n=1036800, precision=0)
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(big), fake, 2, fake, None) == -5
+    assert b"scratch" in lib.lisa_td_last_error()
+    ok = api.make_config(dt=5.0, n=17280, precision=0)
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), fake, 80, fake, None) == -5
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), fake, 3, fake, None) == -1
+    assert b"even" in lib.lisa_td_last_error()
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), None, 2, fake, None) == -1
+
+
+def _walkers(cfg, w, seed):
+    return workloads.prior_draws(w, cfg["n"], cfg["dt"], seed, logm=(5.5, 7.0))
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,precision", [("c1_fp64_1d", 0), ("c2_hm_1d", 1)])
+def test_noalloc_matches_loglike_batch_on_two_calls(name, precision):
+    from paper_2501_08261_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    cfg = workloads.config(name)
+    kw = gpu_kwargs(cfg)
+    ref = api.Likelihood(precision=0, max_walkers=8, **kw)
+    lk = api.Likelihood(precision=precision, max_walkers=8, **kw)
+    truth = _walkers(cfg, 1, 71)
+    d = ref.tdi(ref.project(_t(truth)))[:, :, 0].contiguous()     # zero-noise injection
+    lk.set_data(d)
+    if precision == 0:
+        def close(g, o):
+            return abs(g - o) <= max(1e-6, 1e-11 * abs(o))     # the FP64 tests' bar
+    else:
+        def close(g, o):
+            return abs(g - o) <= max(0.05, 1e-4 * abs(o))      # the mixed tests' bar
+    for call, (W, seed) in enumerate(((6, 72), (4, 73))):    # two calls in a row
+        th = _walkers(cfg, W, seed)
+        th[0] = truth[0]
+        want = lk.loglike(_t(th)).cpu().numpy()
+        r = (lk.tdi(lk.project(_t(th))) - d.to(lk.dtype)[:, :, None]).contiguous()
+        got = torch.full((W,), float("nan"), dtype=torch.float64, device="cuda")
+        api.lisa_td_residual_loglike_noalloc(lk.cfg, r, W, got)
+        got = got.cpu().numpy()
+        assert np.all(np.isfinite(got)), (call, got)
+        for w in range(W):
+            assert close(got[w], want[w]), (call, w, got[w], want[w])
+    lk.close()
+    ref.close()
