@@ -33,6 +33,12 @@ K_TAPS = 32
 FLOPS_PROJECT = 9 * (2 * 2 * K_TAPS + 4 * K_TAPS) + 6 * 32 + 9 * 5        # 2541
 FLOPS_TDI2 = 42 * 2 * K_TAPS + 6 + 10                                     # 2704
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5, max clock
+# DRAM bytes (read + write) per walker-sample of each kernel, from one ncu
+# capture of 30 d x 64 walkers (profiles/tdi_mixed_kernel_30d_64w.md,
+# profiles/project_mixed_kernel_30d_64w.md); traffic scales with walker-samples.
+# Set an entry to None when its kernel changes after the capture.
+NCU_BYTES_PER_UNIT = {"tdi": 1222.564608e6 / (518400 * 64),
+                      "project": 1218.176512e6 / (518400 * 64)}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -265,7 +271,10 @@ def run_ours(args):
         ach = flops_unit * walker_samples / (per_call[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
                 "peak": round(FP32_PEAK_TFLOPS, 2), "unit": "TFLOP/s",
-                "frac": round(ach / FP32_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(ach / FP32_PEAK_TFLOPS, 4),
+                "traffic": (round(NCU_BYTES_PER_UNIT[dom] * walker_samples)
+                            if NCU_BYTES_PER_UNIT.get(dom) else None),
+                "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 30 d x 64 walkers)",
                 "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal)"}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "logL evals/s", "n_gpus": ws,
