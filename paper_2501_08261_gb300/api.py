@@ -14,7 +14,11 @@ LISA_TD_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
-           "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc")
+           "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
+           "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
+           "lisa_gauss_draw", "lisa_gauss_logq", "lisa_mh_accept",
+           "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
+           "flow_logprob", "flow_propose", "flow_grad", "flow_adam", "flow_train", "flow_destroy")
 NSTAGE = 7
 STAGES = ("prep", "waveform", "project", "tdi", "fft_pass1", "fft_pass2_norm", "reduce")
 
@@ -47,6 +51,24 @@ def load_library(path=None):
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
         "lisa_td_residual_loglike_noalloc": ([ctypes.POINTER(Config), P, I32, P, P], ctypes.c_int),
+        "lisa_fisher_npoints": ([I32], ctypes.c_int),
+        "lisa_fisher_points": ([P, P, P, I32, P, P], ctypes.c_int),
+        "lisa_fisher_assemble": ([P, P, I32, P, P], ctypes.c_int),
+        "lisa_cholesky": ([P, I32, P, P, P], ctypes.c_int),
+        "lisa_gauss_draw": ([P, P, P, I32, P, I32, P, P, P], ctypes.c_int),
+        "lisa_gauss_logq": ([P, P, P, I32, P, I32, P, P], ctypes.c_int),
+        "lisa_mh_accept": ([I32, P, P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "flow_create": ([ctypes.POINTER(P), I32, I32, I32, I32, P, P, P], ctypes.c_int),
+        "flow_nparams": ([P, ctypes.POINTER(I64)], ctypes.c_int),
+        "flow_set_params": ([P, P, P], ctypes.c_int),
+        "flow_get_params": ([P, P, P], ctypes.c_int),
+        "flow_set_frame": ([P, P, P, P], ctypes.c_int),
+        "flow_logprob": ([P, P, I32, P, P], ctypes.c_int),
+        "flow_propose": ([P, P, I32, P, P, P], ctypes.c_int),
+        "flow_grad": ([P, P, I32, P, P, P], ctypes.c_int),
+        "flow_adam": ([P, P, ctypes.c_float, P], ctypes.c_int),
+        "flow_train": ([P, P, I64, I32, I32, ctypes.c_float, P, P], ctypes.c_int),
+        "flow_destroy": ([P], None),
         "lisa_td_destroy": ([P], None),
         "lisa_td_last_error": ([], ctypes.c_char_p),
     }
@@ -145,6 +167,112 @@ def lisa_td_residual_loglike_noalloc(cfg, r, W, logl, stream=None):
     _check(lib().lisa_td_residual_loglike_noalloc(ctypes.byref(cfg), _ptr(r), int(W), _ptr(logl),
                                                   _stream(stream)),
            "lisa_td_residual_loglike_noalloc")
+
+
+def _host_i32(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _host_f64(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def lisa_fisher_npoints(D):
+    return int(lib().lisa_fisher_npoints(int(D)))
+
+
+def lisa_fisher_points(theta0, idx, eps, points, stream=None):
+    (ia, ip), (ea, ep) = _host_i32(idx), _host_f64(eps)
+    _check(lib().lisa_fisher_points(_ptr(theta0), ip, ep, len(ia), _ptr(points), _stream(stream)),
+           "lisa_fisher_points")
+
+
+def lisa_fisher_assemble(logl, eps, fisher, stream=None):
+    ea, ep = _host_f64(eps)
+    _check(lib().lisa_fisher_assemble(_ptr(logl), ep, len(ea), _ptr(fisher), _stream(stream)),
+           "lisa_fisher_assemble")
+
+
+def lisa_cholesky(a, D, l, info, stream=None):
+    _check(lib().lisa_cholesky(_ptr(a), int(D), _ptr(l), _ptr(info), _stream(stream)),
+           "lisa_cholesky")
+
+
+def lisa_gauss_draw(mu, l, idx, z, W, x, logq, stream=None):
+    ia, ip = _host_i32(idx)
+    _check(lib().lisa_gauss_draw(_ptr(mu), _ptr(l), ip, len(ia), _ptr(z), int(W), _ptr(x),
+                                 _ptr(logq), _stream(stream)), "lisa_gauss_draw")
+
+
+def lisa_gauss_logq(mu, l, idx, x, W, logq, stream=None):
+    ia, ip = _host_i32(idx)
+    _check(lib().lisa_gauss_logq(_ptr(mu), _ptr(l), ip, len(ia), _ptr(x), int(W), _ptr(logq),
+                                 _stream(stream)), "lisa_gauss_logq")
+
+
+def lisa_mh_accept(W, x_prop, logl_prop, logq_prop, u, lo, hi, x, logl, logq, accepted=None,
+                   stream=None):
+    (la, lp), (ha, hp) = _host_f64(lo), _host_f64(hi)
+    _check(lib().lisa_mh_accept(int(W), _ptr(x_prop), _ptr(logl_prop), _ptr(logq_prop), _ptr(u),
+                                lp, hp, _ptr(x), _ptr(logl), _ptr(logq), _ptr(accepted),
+                                _stream(stream)), "lisa_mh_accept")
+
+
+def flow_create(dim, layers, hidden, max_batch, idx, perms, stream=None):
+    h = ctypes.c_void_p()
+    (ia, ip), (pa, pp) = _host_i32(idx), _host_i32(perms)
+    _check(lib().flow_create(ctypes.byref(h), int(dim), int(layers), int(hidden), int(max_batch),
+                             ip, pp, _stream(stream)), "flow_create")
+    return h
+
+
+def flow_nparams(f):
+    n = ctypes.c_int64()
+    _check(lib().flow_nparams(f, ctypes.byref(n)), "flow_nparams")
+    return n.value
+
+
+def flow_set_params(f, params, stream=None):
+    _check(lib().flow_set_params(f, _ptr(params), _stream(stream)), "flow_set_params")
+
+
+def flow_get_params(f, params, stream=None):
+    _check(lib().flow_get_params(f, _ptr(params), _stream(stream)), "flow_get_params")
+
+
+def flow_set_frame(f, mu, scale, stream=None):
+    _check(lib().flow_set_frame(f, _ptr(mu), _ptr(scale), _stream(stream)), "flow_set_frame")
+
+
+def flow_logprob(f, x, W, logq, stream=None):
+    _check(lib().flow_logprob(f, _ptr(x), int(W), _ptr(logq), _stream(stream)), "flow_logprob")
+
+
+def flow_propose(f, z, W, x, logq, stream=None):
+    _check(lib().flow_propose(f, _ptr(z), int(W), _ptr(x), _ptr(logq), _stream(stream)),
+           "flow_propose")
+
+
+def flow_grad(f, x, B, loss=None, grad=None, stream=None):
+    _check(lib().flow_grad(f, _ptr(x), int(B), _ptr(loss), _ptr(grad), _stream(stream)),
+           "flow_grad")
+
+
+def flow_adam(f, grad, lr, stream=None):
+    _check(lib().flow_adam(f, _ptr(grad), float(lr), _stream(stream)), "flow_adam")
+
+
+def flow_train(f, samples, S, epochs, batch, lr, loss=None, stream=None):
+    _check(lib().flow_train(f, _ptr(samples), int(S), int(epochs), int(batch), float(lr),
+                            _ptr(loss), _stream(stream)), "flow_train")
+
+
+def flow_destroy(f):
+    lib().flow_destroy(f)
 
 
 def lisa_td_destroy(ctx):

@@ -12,9 +12,15 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "lisa_td.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lisa_td_\w+|flow_\w+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(inc, h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(lisa_\w+|flow_\w+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -58,3 +64,17 @@ def test_argument_errors_need_no_gpu(libpath):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         api.load_library(str(tmp_path / "nope.so"))
+
+
+def test_flow_and_sampler_argument_errors_need_no_gpu(libpath):
+    lib = api.load_library(libpath)
+    h = ctypes.c_void_p()
+    idx = (ctypes.c_int32 * 15)(*range(15))
+    perm = (ctypes.c_int32 * 15)(*range(15))
+    assert lib.flow_create(ctypes.byref(h), 16, 1, 128, 64, idx, perm, None) == -1
+    assert lib.flow_create(ctypes.byref(h), 15, 1, 64, 64, idx, perm, None) == -1
+    assert b"128" in lib.lisa_td_last_error()
+    bad = (ctypes.c_int32 * 15)(*([0] * 15))
+    assert lib.flow_create(ctypes.byref(h), 15, 1, 128, 64, bad, perm, None) == -1
+    assert lib.lisa_fisher_npoints(15) == 451
+    assert lib.lisa_cholesky(None, 3, None, None, None) == -1
