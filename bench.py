@@ -298,6 +298,15 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, theta[0], aet.cpu().numpy())
+    if not args.no_proposals:
+        # learned proposal vs the Fisher-Gaussian one, on the exact likelihood
+        from paper_2501_08261_gb300 import proposals
+        r = proposals.compare()
+        out["proposals"] = {
+            "workload": r["workload"],
+            "fisher_gauss": {k: round(r["fisher_gauss"][k], 4) for k in ("acceptance", "ess_per_s", "tau")},
+            "flow": {k: round(r["flow"][k], 4) for k in ("acceptance", "ess_per_s", "tau", "train_ms")},
+            "unit": "effective samples/s (GPU time, integrated autocorrelation, Sokal window)"}
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -351,6 +360,8 @@ def main():
     ap.add_argument("--walkers", type=int, default=WALKERS)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--no-proposals", action="store_true",
+                    help="skip the flow vs Fisher-Gaussian proposal measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

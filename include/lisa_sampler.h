@@ -46,11 +46,14 @@ int lisa_fisher_points(const double* theta0_dev, const int32_t* idx_host,
 int lisa_fisher_assemble(const double* logl_dev, const double* eps_host, int32_t D,
                          double* fisher_dev, void* stream);
 
-/* Cholesky factor: lower-triangular l_dev [D][D] with L L^T = a_dev [D][D]
- * (FP64, upper triangle of l set to 0).  info_dev [1]: 0, or j + 1 if the
+/* Cholesky factor: lower-triangular l_dev [D][D] with
+ * L L^T = a_dev [D][D] + diag(diag_host) (FP64, upper triangle of l set to 0).
+ * diag_host [D] >= 0 or NULL; the sampler passes the precision 12 / w^2 of
+ * each uniform prior of width w, so that directions the data leave
+ * unconstrained take the prior's width.  info_dev [1]: 0, or j + 1 if the
  * leading (j+1) x (j+1) block is not positive definite (L then partial). */
-int lisa_cholesky(const double* a_dev, int32_t D, double* l_dev, int32_t* info_dev,
-                  void* stream);
+int lisa_cholesky(const double* a_dev, const double* diag_host, int32_t D, double* l_dev,
+                  int32_t* info_dev, void* stream);
 
 /* Gaussian proposal q = N(mu, F^-1) with F = L L^T: for each of W walkers,
  * x = mu + L^-T z on the sampled parameters (others = mu), and
@@ -60,6 +63,12 @@ int lisa_cholesky(const double* a_dev, int32_t D, double* l_dev, int32_t* info_d
 int lisa_gauss_draw(const double* mu_dev, const double* l_dev, const int32_t* idx_host,
                     int32_t D, const double* z_dev, int32_t W, double* x_dev, double* logq_dev,
                     void* stream);
+
+/* Random-walk proposal with the Fisher covariance: x' = x + step L^-T z for
+ * each walker (x_dev, x_prop_dev [W][15], z_dev [W][D]); symmetric, so the
+ * accept step takes log q = 0 for both positions. */
+int lisa_gauss_walk(const double* x_dev, const double* l_dev, const int32_t* idx_host, int32_t D,
+                    const double* z_dev, int32_t W, double step, double* x_prop_dev, void* stream);
 
 /* log q(x) of the same Gaussian at given positions x_dev [W][15]. */
 int lisa_gauss_logq(const double* mu_dev, const double* l_dev, const int32_t* idx_host,

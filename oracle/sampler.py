@@ -89,6 +89,16 @@ def gauss_logq(mu, L, idx, x):
     return -0.5 * np.sum(z * z, axis=1) + np.sum(np.log(np.diag(L))) - 0.5 * D * math.log(2 * math.pi)
 
 
+def gauss_walk(x, L, idx, z, step):
+    """Random-walk proposal x' = x + step L^-T z on the sampled parameters
+    (symmetric: log q terms cancel, pass log q = 0 to mh_accept)."""
+    x = np.array(np.atleast_2d(x), dtype=np.float64)
+    z = np.atleast_2d(np.asarray(z, dtype=np.float64))
+    y = solve_triangular(L.T, z.T, lower=False).T
+    x[:, idx] += step * y
+    return x
+
+
 def mh_accept(x, logl, logq, xp, loglp, logqp, u, lo, hi):
     """One independence Metropolis-Hastings decision per walker.
     -> (x, logl, logq) after the step and the accepted flags (int)."""

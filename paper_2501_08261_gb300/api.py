@@ -16,7 +16,7 @@ EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_pr
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
-           "lisa_gauss_draw", "lisa_gauss_logq", "lisa_mh_accept",
+           "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept",
            "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
            "flow_logprob", "flow_propose", "flow_grad", "flow_adam", "flow_train", "flow_destroy")
 NSTAGE = 7
@@ -54,9 +54,10 @@ def load_library(path=None):
         "lisa_fisher_npoints": ([I32], ctypes.c_int),
         "lisa_fisher_points": ([P, P, P, I32, P, P], ctypes.c_int),
         "lisa_fisher_assemble": ([P, P, I32, P, P], ctypes.c_int),
-        "lisa_cholesky": ([P, I32, P, P, P], ctypes.c_int),
+        "lisa_cholesky": ([P, P, I32, P, P, P], ctypes.c_int),
         "lisa_gauss_draw": ([P, P, P, I32, P, I32, P, P, P], ctypes.c_int),
         "lisa_gauss_logq": ([P, P, P, I32, P, I32, P, P], ctypes.c_int),
+        "lisa_gauss_walk": ([P, P, P, I32, P, I32, ctypes.c_double, P, P], ctypes.c_int),
         "lisa_mh_accept": ([I32, P, P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "flow_create": ([ctypes.POINTER(P), I32, I32, I32, I32, P, P, P], ctypes.c_int),
         "flow_nparams": ([P, ctypes.POINTER(I64)], ctypes.c_int),
@@ -197,8 +198,12 @@ def lisa_fisher_assemble(logl, eps, fisher, stream=None):
            "lisa_fisher_assemble")
 
 
-def lisa_cholesky(a, D, l, info, stream=None):
-    _check(lib().lisa_cholesky(_ptr(a), int(D), _ptr(l), _ptr(info), _stream(stream)),
+def lisa_cholesky(a, D, l, info, diag=None, stream=None):
+    if diag is None:
+        dp = None
+    else:
+        da, dp = _host_f64(diag)
+    _check(lib().lisa_cholesky(_ptr(a), dp, int(D), _ptr(l), _ptr(info), _stream(stream)),
            "lisa_cholesky")
 
 
@@ -212,6 +217,12 @@ def lisa_gauss_logq(mu, l, idx, x, W, logq, stream=None):
     ia, ip = _host_i32(idx)
     _check(lib().lisa_gauss_logq(_ptr(mu), _ptr(l), ip, len(ia), _ptr(x), int(W), _ptr(logq),
                                  _stream(stream)), "lisa_gauss_logq")
+
+
+def lisa_gauss_walk(x, l, idx, z, W, step, x_prop, stream=None):
+    ia, ip = _host_i32(idx)
+    _check(lib().lisa_gauss_walk(_ptr(x), _ptr(l), ip, len(ia), _ptr(z), int(W), float(step),
+                                 _ptr(x_prop), _stream(stream)), "lisa_gauss_walk")
 
 
 def lisa_mh_accept(W, x_prop, logl_prop, logq_prop, u, lo, hi, x, logl, logq, accepted=None,

@@ -67,13 +67,13 @@ __global__ void fisher_assemble_kernel(const double* __restrict__ logl, SampleSp
   F[b * D + a] = f;
 }
 
-__global__ void cholesky_kernel(const double* __restrict__ A, int D, double* __restrict__ L,
-                                int32_t* info) {
+__global__ void cholesky_kernel(const double* __restrict__ A, SampleSpec dg, int D,
+                                double* __restrict__ L, int32_t* info) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
   for (int q = 0; q < D * D; ++q) L[q] = 0.0;
   int bad = 0;
   for (int j = 0; j < D && !bad; ++j) {
-    double s = A[j * D + j];
+    double s = A[j * D + j] + dg.eps[j];
     for (int k = 0; k < j; ++k) s -= L[j * D + k] * L[j * D + k];
     if (!(s > 0.0)) {
       bad = j + 1;
@@ -116,6 +116,22 @@ __global__ void gauss_draw_kernel(const double* __restrict__ mu, const double* _
   for (int k = 0; k < kP; ++k) x[(int64_t)w * kP + k] = mu[k];
   for (int i = 0; i < D; ++i) x[(int64_t)w * kP + sp.idx[i]] = mu[sp.idx[i]] + y[i];
   logq[w] = -0.5 * q2 + log_norm_const(L, D);
+}
+
+__global__ void gauss_walk_kernel(const double* __restrict__ x, const double* __restrict__ L,
+                                  SampleSpec sp, const double* __restrict__ z, int W, double step,
+                                  double* __restrict__ xp) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  const int D = sp.D;
+  double y[kP];
+  for (int i = D - 1; i >= 0; --i) {            // L^T y = z
+    double t = z[(int64_t)w * D + i];
+    for (int k = i + 1; k < D; ++k) t -= L[k * D + i] * y[k];
+    y[i] = t / L[i * D + i];
+  }
+  for (int k = 0; k < kP; ++k) xp[(int64_t)w * kP + k] = x[(int64_t)w * kP + k];
+  for (int i = 0; i < D; ++i) xp[(int64_t)w * kP + sp.idx[i]] += step * y[i];
 }
 
 __global__ void gauss_logq_kernel(const double* __restrict__ mu, const double* __restrict__ L,
@@ -215,10 +231,18 @@ int lisa_fisher_assemble(const double* logl_dev, const double* eps_host, int32_t
   return launched("lisa_fisher_assemble");
 }
 
-int lisa_cholesky(const double* a_dev, int32_t D, double* l_dev, int32_t* info_dev, void* stream) {
+int lisa_cholesky(const double* a_dev, const double* diag_host, int32_t D, double* l_dev,
+                  int32_t* info_dev, void* stream) {
   if (!a_dev || !l_dev || !info_dev) return report_error(LISA_TD_EINVAL, "NULL argument");
   if (D < 1 || D > kP) return report_error(LISA_TD_EINVAL, "D=%d must be in 1..15", D);
-  cholesky_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(a_dev, D, l_dev, info_dev);
+  SampleSpec dg;
+  memset(&dg, 0, sizeof(dg));
+  if (diag_host)
+    for (int j = 0; j < D; ++j) {
+      if (!(diag_host[j] >= 0.0) || !isfinite(diag_host[j])) return report_error(LISA_TD_EINVAL, "diag[%d] must be >= 0", j);
+      dg.eps[j] = diag_host[j];
+    }
+  cholesky_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(a_dev, dg, D, l_dev, info_dev);
   return launched("lisa_cholesky");
 }
 
@@ -233,6 +257,20 @@ int lisa_gauss_draw(const double* mu_dev, const double* l_dev, const int32_t* id
   gauss_draw_kernel<<<nb(W, 128), 128, 0, (cudaStream_t)stream>>>(mu_dev, l_dev, sp, z_dev, W,
                                                                   x_dev, logq_dev);
   return launched("lisa_gauss_draw");
+}
+
+int lisa_gauss_walk(const double* x_dev, const double* l_dev, const int32_t* idx_host, int32_t D,
+                    const double* z_dev, int32_t W, double step, double* x_prop_dev, void* stream) {
+  if (!x_dev || !l_dev || !idx_host || !z_dev || !x_prop_dev)
+    return report_error(LISA_TD_EINVAL, "NULL argument");
+  if (W < 1) return report_error(LISA_TD_EINVAL, "W must be >= 1");
+  if (!(step > 0.0)) return report_error(LISA_TD_EINVAL, "step must be > 0");
+  SampleSpec sp;
+  int rc = spec_from(idx_host, nullptr, D, &sp);
+  if (rc) return rc;
+  gauss_walk_kernel<<<nb(W, 128), 128, 0, (cudaStream_t)stream>>>(x_dev, l_dev, sp, z_dev, W, step,
+                                                                  x_prop_dev);
+  return launched("lisa_gauss_walk");
 }
 
 int lisa_gauss_logq(const double* mu_dev, const double* l_dev, const int32_t* idx_host, int32_t D,

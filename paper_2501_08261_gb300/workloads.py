@@ -109,6 +109,18 @@ def table1_precessing(n, dt, tc_frac=0.9):
                      r(149.0), r(229.2), r(-34.4), r(34.4), r(22.9), tc_frac * n * dt])
 
 
+def table1_prior_box(tc, tc_halfwidth=600.0):
+    """Uniform prior ranges of Table I (precessing columns, degrees -> radians),
+    as (lo [15], hi [15]) in the parameter order; the merger-time range
+    (t_c +- tc_halfwidth seconds) is not in Table I and is declared here."""
+    r = math.radians
+    lo = np.array([0.99e6, 0.69e6, 0.0, 0.0, r(-180.0), 0.0, 0.0, r(-180.0), 19.0, 0.0, 0.0,
+                   r(-180.0), 0.0, r(-180.0), tc - tc_halfwidth])
+    hi = np.array([1.01e6, 0.71e6, 1.0, r(180.0), r(180.0), 1.0, r(180.0), r(180.0), 21.0,
+                   r(180.0), r(360.0), r(180.0), r(360.0), r(180.0), tc + tc_halfwidth])
+    return lo, hi
+
+
 def standard_normals(w, dim, seed):
     """Standard normal draws (used as z in theta + L z perturbations)."""
     return np.random.default_rng(seed).normal(size=(w, dim))

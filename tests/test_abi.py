@@ -77,4 +77,4 @@ def test_flow_and_sampler_argument_errors_need_no_gpu(libpath):
     bad = (ctypes.c_int32 * 15)(*([0] * 15))
     assert lib.flow_create(ctypes.byref(h), 15, 1, 128, 64, bad, perm, None) == -1
     assert lib.lisa_fisher_npoints(15) == 451
-    assert lib.lisa_cholesky(None, 3, None, None, None) == -1
+    assert lib.lisa_cholesky(None, None, 3, None, None, None) == -1

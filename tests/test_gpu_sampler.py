@@ -59,6 +59,14 @@ def test_cholesky_matches_library_and_flags_indefinite():
         assert info.item() == 0
         assert np.max(np.abs(Lg - sampler.cholesky(A))) <= 1e-13 * np.max(np.abs(Lg))
         assert np.all(np.triu(Lg, 1) == 0.0)
+    # a diagonal added before factorising (prior precision)
+    A = _spd(6, 11)
+    dg = np.linspace(0.5, 3.0, 6)
+    L = torch.empty((6, 6), dtype=torch.float64, device="cuda")
+    info = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    api.lisa_cholesky(_t(A), 6, L, info, diag=dg)
+    assert info.item() == 0
+    assert np.max(np.abs(L.cpu().numpy() - sampler.cholesky(A + np.diag(dg)))) <= 1e-13 * np.max(np.abs(A))
     B = _spd(4, 9)
     B[2, 2] = -1.0
     L = torch.empty((4, 4), dtype=torch.float64, device="cuda")
@@ -83,6 +91,20 @@ def test_gauss_draw_and_logq_match_oracle():
     lq2 = torch.empty(W, dtype=torch.float64, device="cuda")
     api.lisa_gauss_logq(_t(mu), _t(L), idx, _t(xo), W, lq2)
     assert np.max(np.abs(lq2.cpu().numpy() - sampler.gauss_logq(mu, L, idx, xo))) <= 1e-12 * np.max(np.abs(lqo))
+
+
+def test_gauss_walk_matches_oracle():
+    D, W = 6, 500
+    F = _spd(D, 23)
+    L = sampler.cholesky(F)
+    idx = [1, 3, 5, 7, 9, 14]
+    rng = np.random.default_rng(24)
+    x = rng.normal(size=(W, 15))
+    z = rng.normal(size=(W, D))
+    xp = torch.empty((W, 15), dtype=torch.float64, device="cuda")
+    api.lisa_gauss_walk(_t(x), _t(L), idx, _t(z), W, 0.7, xp)
+    want = sampler.gauss_walk(x, L, idx, z, 0.7)
+    assert np.max(np.abs(xp.cpu().numpy() - want)) <= 1e-13 * np.max(np.abs(want))
 
 
 def test_mh_accept_decisions_match_oracle_exactly():

@@ -136,3 +136,30 @@ def test_mh_rejects_outside_box_and_minus_infinity():
     xn, ln, qn, acc = sampler.mh_accept(x, logl, logq, xp, loglp, np.zeros(W), u, lo, hi)
     assert acc[0] == 0 and acc[1] == 0 and np.all(acc[2:] == 1)
     assert np.all(xn[0] == 0.0) and ln[1] == -5.0 and ln[7] == 10.0
+
+
+def test_random_walk_chain_targets_a_correlated_gaussian():
+    # target N(0, C) in 2-d through the Fisher factor of C^-1: stationary moments
+    C = np.array([[1.0, 0.8], [0.8, 1.0]])
+    L = sampler.cholesky(np.linalg.inv(C))
+    rng = np.random.default_rng(8)
+    W, idx = 256, [2, 9]
+    lo, hi = np.full(15, -50.0), np.full(15, 50.0)
+    Ci = np.linalg.inv(C)
+
+    def logl_of(x):
+        y = x[:, idx]
+        return -0.5 * np.einsum("wi,ij,wj->w", y, Ci, y)
+
+    x = np.zeros((W, 15))
+    logl, zero = logl_of(x), np.zeros(W)
+    keep = []
+    for it in range(800):
+        xp = sampler.gauss_walk(x, L, idx, rng.normal(size=(W, 2)), 2.38 / np.sqrt(2))
+        x, logl, _, _ = sampler.mh_accept(x, logl, zero, xp, logl_of(xp), zero,
+                                          rng.uniform(1e-300, 1.0, W), lo, hi)
+        if it >= 200:
+            keep.append(x[:, idx].copy())
+    s = np.concatenate(keep)
+    assert np.allclose(np.cov(s.T), C, atol=0.06)
+    assert np.all(np.abs(s.mean(axis=0)) < 0.05)
