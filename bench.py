@@ -112,6 +112,25 @@ def _gpu_kwargs(cfg):
                 mode_mask=cfg["mode_mask"], precessing=cfg["precessing"])
 
 
+def walker_seed(rank):
+    """Each rank draws its own walkers (weak scaling: W walkers per GPU, no
+    exchange between ranks inside a likelihood)."""
+    return 1000 + rank
+
+
+def max_over_ranks(torch, dist, values, device=None):
+    """Timings reduced with MAX over ranks (the job is as slow as its slowest rank)."""
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_throughput(W, world_size, steps, ms_max):
+    """Whole-job logL evals/s: all ranks' walkers over the slowest rank's time."""
+    return W * world_size * steps / (ms_max * 1e-3)
+
+
 def _time_steps(torch, fn, steps, barrier):
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -189,7 +208,7 @@ def run_ours(args):
     cfg = workloads.config(args.workload)
     kw = _gpu_kwargs(cfg)
     W = args.walkers
-    theta = workloads.prior_draws(W, cfg["n"], cfg["dt"], seed=1000 + rank)
+    theta = workloads.prior_draws(W, cfg["n"], cfg["dt"], seed=walker_seed(rank))
     dev = torch.device("cuda", lrank)
     params = torch.as_tensor(theta, device=dev)
     lk32 = api.Likelihood(precision=1, max_walkers=W, **kw)
@@ -241,16 +260,13 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_e2e = _time_steps(torch, step_e2e, args.steps, barrier)
     # max over ranks
-    t32 = torch.tensor([ms32, ms64, ms_e2e], device=dev)
-    if dist is not None:
-        dist.all_reduce(t32, op=dist.ReduceOp.MAX)
-    ms32, ms64, ms_e2e = (float(x) for x in t32.tolist())
+    ms32, ms64, ms_e2e = max_over_ranks(torch, dist, [ms32, ms64, ms_e2e], dev)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
     evals = W * ws
-    value = evals * args.steps / (ms32 * 1e-3)
+    value = job_throughput(W, ws, args.steps, ms32)
     cmp = None
     if l64 is not None:
         d = (l32 - l64).abs().cpu().numpy()
