@@ -100,6 +100,27 @@ int lisa_td_tdi(lisa_td_ctx* ctx, const void* y_dev, int32_t W, void* aet_dev,
 int lisa_td_loglike_batch(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
                           double* logl_dev, int32_t* status_dev, void* stream);
 
+/* Ragged batch (walkers of uneven signal length): walker w is evaluated on
+ * its own analysis window, the last n_host[w] samples of the grid (times
+ * t0 + (n - n_w + j) dt, j < n_w), with the data restricted to that window
+ * and its own DFT of length n_w (frequency resolution 1 / (n_w dt)); the
+ * result is what lisa_td_loglike_batch gives on a context whose grid is that
+ * window.  n_host [W] (host): multiples of 64, 2^a 3^b 5^c 7^d, in [128, n];
+ * cfg.n must be a multiple of 64.  Walkers are grouped by window length; the
+ * first call with a new length allocates that length's FFT plan, PSD weights
+ * and data window (kept until lisa_td_destroy).  Rewriting the order of
+ * walkers needs the previous call's upload of it to have completed, which
+ * the call waits for. */
+int lisa_td_loglike_ragged(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
+                           const int64_t* n_host, double* logl_dev, int32_t* status_dev,
+                           void* stream);
+
+/* With enable = 1, lisa_td_loglike_ragged captures its whole launch sequence
+ * (all length classes) in a CUDA graph on first use of a given class
+ * histogram and pointer set, and replays it while they repeat (needs a
+ * non-default stream; on the legacy stream it runs uncaptured). */
+int lisa_td_ragged_graph(lisa_td_ctx* ctx, int32_t enable);
+
 /* Stage timing of lisa_td_loglike_batch (measurement support, no paper
  * counterpart).  lisa_td_profile(ctx, 1) makes the following loglike calls
  * record a CUDA event on their stream before each stage and after the last

@@ -15,6 +15,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
+           "lisa_td_loglike_ragged", "lisa_td_ragged_graph",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
            "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept",
            "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
@@ -47,6 +48,8 @@ def load_library(path=None):
         "lisa_td_project": ([P, P, I32, P, P], ctypes.c_int),
         "lisa_td_tdi": ([P, P, I32, P, P], ctypes.c_int),
         "lisa_td_loglike_batch": ([P, P, I32, P, P, P], ctypes.c_int),
+        "lisa_td_loglike_ragged": ([P, P, I32, P, P, P, P], ctypes.c_int),
+        "lisa_td_ragged_graph": ([P, I32], ctypes.c_int),
         "lisa_td_profile": ([P, I32], ctypes.c_int),
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
@@ -147,6 +150,18 @@ def lisa_td_tdi(ctx, y, W, aet, stream=None):
 def lisa_td_loglike_batch(ctx, params, W, logl, status=None, stream=None):
     _check(lib().lisa_td_loglike_batch(ctx, _ptr(params), int(W), _ptr(logl), _ptr(status),
                                        _stream(stream)), "lisa_td_loglike_batch")
+
+
+def lisa_td_loglike_ragged(ctx, params, W, n_per_walker, logl, status=None, stream=None):
+    import numpy as np
+    nh = np.ascontiguousarray(n_per_walker, dtype=np.int64)
+    _check(lib().lisa_td_loglike_ragged(ctx, _ptr(params), int(W),
+                                        nh.ctypes.data_as(ctypes.c_void_p), _ptr(logl),
+                                        _ptr(status), _stream(stream)), "lisa_td_loglike_ragged")
+
+
+def lisa_td_ragged_graph(ctx, enable):
+    _check(lib().lisa_td_ragged_graph(ctx, int(enable)), "lisa_td_ragged_graph")
 
 
 def lisa_td_profile(ctx, enable):
@@ -354,6 +369,14 @@ class Likelihood:
         aet = self.torch.empty((3, self.cfg.n, W), dtype=self.dtype, device=y.device)
         lisa_td_tdi(self.ctx, y, W, aet)
         return aet
+
+    def loglike_ragged(self, params, n_per_walker, with_status=False, stream=None):
+        params = self._params(params)
+        W = params.shape[0]
+        out = self.torch.empty(W, dtype=self.torch.float64, device=params.device)
+        st = self.torch.empty(W, dtype=self.torch.int32, device=params.device)
+        lisa_td_loglike_ragged(self.ctx, params, W, n_per_walker, out, st, stream)
+        return (out, st) if with_status else out
 
     def loglike(self, params, with_status=False):
         params = self._params(params)

@@ -35,6 +35,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 void free_ctx(lisa_td_ctx* c) {
   if (!c) return;
+  lisa::free_ragged(c);
   if (c->prof_ev) {
     for (int q = 0; q < LISA_TD_PROF_CALLS * (LISA_TD_NSTAGE + 1); ++q)
       if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);
@@ -77,6 +78,28 @@ inline int pad32(int w) { return (w + 31) / 32 * 32; }
 }  // namespace
 
 namespace lisa {
+
+cudaError_t run_loglike_stages(const lisa_td_ctx* c, const double* params, int W, double* logl,
+                               int32_t* status, cudaStream_t s, cudaEvent_t* ev) {
+  const int Wp = pad32(W);
+  cudaError_t e = cudaSuccess;
+#define STAGE(k, call)                                   \
+  do {                                                   \
+    if (ev && (e = cudaEventRecord(ev[k], s)) != cudaSuccess) return e; \
+    if ((e = (call)) != cudaSuccess) return e;           \
+  } while (0)
+  STAGE(0, launch_prep(c, params, W, Wp, s));
+  STAGE(1, launch_waveform(c, Wp, c->h, s));
+  STAGE(2, launch_project(c, Wp, Wp, c->h, c->y, s));
+  STAGE(3, launch_tdi(c, Wp, Wp, c->y, c->r, 1, s));
+  STAGE(4, launch_fft_pass1(c, Wp, c->r, s));
+  STAGE(5, launch_fft_pass2(c, Wp, s));
+  STAGE(6, launch_reduce(c, W, Wp, logl, status, s));
+#undef STAGE
+  if (ev) e = cudaEventRecord(ev[LISA_TD_NSTAGE], s);
+  return e;
+}
+
 int report_error(int code, const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -170,6 +193,7 @@ int lisa_td_set_data(lisa_td_ctx* c, const double* aet_dev, void* stream) {
   CK(lisa::launch_data_copy(c, aet_dev, s), "lisa_td_set_data");
   CK(cudaStreamSynchronize(s), "lisa_td_set_data");
   c->has_data = 1;
+  c->data_version += 1;
   return LISA_TD_OK;
 }
 
@@ -216,24 +240,10 @@ int lisa_td_loglike_batch(lisa_td_ctx* c, const double* params_dev, int32_t W, d
   if (rc) return rc;
   if (!c->has_data) return fail(LISA_TD_EINVAL, "lisa_td_set_data has not been called");
   cudaStream_t s = (cudaStream_t)stream;
-  const int Wp = pad32(W);
   cudaEvent_t* ev = nullptr;
   if (c->prof_on && c->prof_calls < LISA_TD_PROF_CALLS)
     ev = c->prof_ev + (size_t)(c->prof_calls++) * (LISA_TD_NSTAGE + 1);
-#define STAGE(k, call, what)                                \
-  do {                                                      \
-    if (ev) CK(cudaEventRecord(ev[k], s), "loglike: event"); \
-    CK(call, what);                                         \
-  } while (0)
-  STAGE(0, lisa::launch_prep(c, params_dev, W, Wp, s), "loglike: prep");
-  STAGE(1, lisa::launch_waveform(c, Wp, c->h, s), "loglike: waveform");
-  STAGE(2, lisa::launch_project(c, Wp, Wp, c->h, c->y, s), "loglike: project");
-  STAGE(3, lisa::launch_tdi(c, Wp, Wp, c->y, c->r, 1, s), "loglike: tdi");
-  STAGE(4, lisa::launch_fft_pass1(c, Wp, c->r, s), "loglike: fft pass 1");
-  STAGE(5, lisa::launch_fft_pass2(c, Wp, s), "loglike: fft pass 2");
-  STAGE(6, lisa::launch_reduce(c, W, Wp, logl_dev, status_dev, s), "loglike: reduce");
-#undef STAGE
-  if (ev) CK(cudaEventRecord(ev[LISA_TD_NSTAGE], s), "loglike: event");
+  CK(lisa::run_loglike_stages(c, params_dev, W, logl_dev, status_dev, s, ev), "lisa_td_loglike_batch");
   return LISA_TD_OK;
 }
 

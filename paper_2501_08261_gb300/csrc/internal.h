@@ -51,6 +51,10 @@ struct lisa_td_ctx {
   int prof_on;
   int prof_calls;
   cudaEvent_t* prof_ev;            // [LISA_TD_PROF_CALLS][LISA_TD_NSTAGE + 1]
+  // ragged batches (ragged.cu): window views and their workspace; data version
+  // bumped by lisa_td_set_data so that the views refresh their data windows
+  void* ragged;
+  int data_version;
 };
 
 namespace lisa {
@@ -79,6 +83,11 @@ cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl,
 int plan_fft(int64_t n, FftPlan* p);
 // api.cu: set the thread's lisa_td_last_error() text, return `code`
 int report_error(int code, const char* fmt, ...);
+// ragged.cu: release the window views of a context
+void free_ragged(lisa_td_ctx* c);
+// the seven stages of one likelihood evaluation on context (or view) c
+cudaError_t run_loglike_stages(const lisa_td_ctx* c, const double* params, int W, double* logl,
+                               int32_t* status, cudaStream_t s, cudaEvent_t* ev);
 TdiTable build_tdi_table(int gen);
 cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s);
 

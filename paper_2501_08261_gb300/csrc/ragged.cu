@@ -1,0 +1,318 @@
+// Ragged batches (lisa_td_loglike_ragged): walkers whose analysis windows have
+// different lengths.  Walker w is evaluated on the last n_w samples of the
+// context's grid -- its own likelihood on that window, with its own DFT
+// length and frequency resolution 1 / (n_w dt).
+//
+// Design: walkers are grouped by window length ("length classes"); each class
+// runs the seven likelihood stages on a window view of the context.  A view
+// shares the context's orbit tables and TDI tile table by pointer offset (the
+// window starts at sample off = n - n_w, a multiple of the 64-sample TDI
+// tile) and the context's workspace (classes run one after the other on the
+// stream), and owns only what depends on the window length: FFT plan and
+// twiddles, PSD weights, the data window and the norm partials.  Views are
+// created on first use of a length and kept.  With graph capture enabled the
+// whole class sequence is captured once per (class histogram, pointers) and
+// replayed.
+#include <math.h>
+#include <string.h>
+
+#include <map>
+#include <vector>
+
+#include "internal.h"
+
+namespace lisa {
+namespace {
+
+struct View {
+  lisa_td_ctx v;              // shallow copy of the context with window fields replaced
+  int64_t off;
+  int data_version;
+};
+
+struct Ragged {
+  std::map<int64_t, View*> views;
+  int cap;                    // walkers the buffers below hold
+  int32_t* perm_ring[2];      // pinned [cap] each: walker index in class order; two, used in
+  cudaEvent_t perm_ev[2];     // turn, each reused only after its previous upload completed
+  int ring;
+  int32_t* perm_host;         // the ring entry of the current call
+  int32_t* perm_dev;
+  double* params_ws;          // [cap][15]
+  double* logl_ws;            // [cap]
+  int32_t* status_ws;         // [cap]
+  int graph_on;
+  std::vector<int64_t> key;   // class histogram + pointers of the captured graph
+  cudaGraphExec_t exec;
+};
+
+__global__ void view_data_kernel(const double* __restrict__ d64, int64_t n, int64_t off,
+                                 int64_t nv, double* __restrict__ o64, float* __restrict__ o32) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= 3 * nv) return;
+  const int64_t c = id / nv, i = id % nv;
+  const double v = d64[c * n + off + i];
+  o64[id] = v;
+  o32[id] = (float)v;
+}
+
+__global__ void gather_kernel(const double* __restrict__ params, const int32_t* __restrict__ perm,
+                              int start, int Wc, double* __restrict__ out) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= Wc * 15) return;
+  const int k = id / 15, j = id % 15;
+  out[id] = params[(int64_t)perm[start + k] * 15 + j];
+}
+
+__global__ void scatter_kernel(const double* __restrict__ logl_ws, const int32_t* __restrict__ st_ws,
+                               const int32_t* __restrict__ perm, int start, int Wc,
+                               double* __restrict__ logl, int32_t* __restrict__ status) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Wc) return;
+  const int w = perm[start + k];
+  logl[w] = logl_ws[k];
+  if (status) status[w] = st_ws[k];
+}
+
+void free_view(View* vw) {
+  if (!vw) return;
+  void* ptrs[] = {vw->v.plan.tw_n, vw->v.plan.tw1, vw->v.plan.tw2, vw->v.psdw, vw->v.data64,
+                  vw->v.data32, vw->v.partial};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete vw;
+}
+
+Ragged* state(lisa_td_ctx* c) {
+  if (!c->ragged) {
+    Ragged* r = new Ragged();
+    r->cap = 0;
+    r->perm_ring[0] = r->perm_ring[1] = nullptr;
+    r->perm_ev[0] = r->perm_ev[1] = nullptr;
+    r->ring = 0;
+    r->perm_host = nullptr;
+    r->perm_dev = nullptr;
+    r->params_ws = nullptr;
+    r->logl_ws = nullptr;
+    r->status_ws = nullptr;
+    r->graph_on = 0;
+    r->exec = nullptr;
+    c->ragged = r;
+  }
+  return (Ragged*)c->ragged;
+}
+
+void release_buffers(Ragged* r) {
+  for (int q = 0; q < 2; ++q) {
+    if (r->perm_ev[q]) {
+      cudaEventSynchronize(r->perm_ev[q]);
+      cudaEventDestroy(r->perm_ev[q]);
+    }
+    if (r->perm_ring[q]) cudaFreeHost(r->perm_ring[q]);
+    r->perm_ring[q] = nullptr;
+    r->perm_ev[q] = nullptr;
+  }
+  void* ptrs[] = {r->perm_dev, r->params_ws, r->logl_ws, r->status_ws};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  r->perm_host = nullptr;
+  r->perm_dev = nullptr;
+  r->params_ws = nullptr;
+  r->logl_ws = nullptr;
+  r->status_ws = nullptr;
+  r->cap = 0;
+}
+
+cudaError_t ensure_buffers(Ragged* r, int W) {
+  if (r->cap >= W) return cudaSuccess;
+  release_buffers(r);
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+    e = cudaMallocHost((void**)&r->perm_ring[q], sizeof(int32_t) * W);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->perm_ev[q], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&r->perm_dev, sizeof(int32_t) * W);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&r->params_ws, sizeof(double) * 15 * W);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&r->logl_ws, sizeof(double) * W);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&r->status_ws, sizeof(int32_t) * W);
+  if (e == cudaSuccess) r->cap = W;
+  return e;
+}
+
+// the view of the last nv samples (created on first use)
+cudaError_t get_view(lisa_td_ctx* c, Ragged* r, int64_t nv, cudaStream_t s, View** out) {
+  auto it = r->views.find(nv);
+  View* vw = it == r->views.end() ? nullptr : it->second;
+  if (!vw) {
+    vw = new View();
+    vw->v = *c;
+    vw->off = c->n - nv;
+    vw->data_version = -1;
+    lisa_td_ctx& v = vw->v;
+    v.n = nv;
+    v.cfg.n = nv;
+    v.cfg.t0 = c->cfg.t0 + (double)vw->off * c->cfg.dt;
+    v.orb64 = c->orb64 + vw->off;
+    v.orb32 = c->orb32 + vw->off;
+    v.tdi_tiles = c->tdi_tiles + (vw->off / kTdiTile) * c->n_dterms;
+    v.prof_ev = nullptr;
+    v.prof_on = 0;
+    v.ragged = nullptr;
+    v.plan.tw_n = v.plan.tw1 = v.plan.tw2 = nullptr;
+    v.psdw = nullptr;
+    v.data64 = nullptr;
+    v.data32 = nullptr;
+    v.partial = nullptr;
+    plan_fft(nv, &v.plan);
+    const size_t cs = 2 * (size_t)c->esize;
+    cudaError_t e = cudaMalloc(&v.plan.tw_n, cs * nv);
+    if (e == cudaSuccess) e = cudaMalloc(&v.plan.tw1, cs * v.plan.n1);
+    if (e == cudaSuccess) e = cudaMalloc(&v.plan.tw2, cs * v.plan.n2);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v.psdw, sizeof(double) * 2 * (nv / 2 + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v.data64, sizeof(double) * 3 * nv);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v.data32, sizeof(float) * 3 * nv);
+    if (e == cudaSuccess)
+      e = cudaMalloc((void**)&v.partial, sizeof(double) * 3 * (v.plan.n1 / 2 + 1) * c->wmax_pad);
+    if (e == cudaSuccess) e = launch_twiddles(&v, s);
+    if (e == cudaSuccess) e = launch_psd_weights(&v, s);
+    if (e != cudaSuccess) {
+      free_view(vw);
+      return e;
+    }
+    r->views[nv] = vw;
+  }
+  if (vw->data_version != c->data_version) {
+    const int64_t m = 3 * nv;
+    view_data_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(c->data64, c->n, vw->off, nv,
+                                                                vw->v.data64, vw->v.data32);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    vw->data_version = c->data_version;
+    vw->v.has_data = 1;
+  }
+  *out = vw;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+void free_ragged(lisa_td_ctx* c) {
+  Ragged* r = (Ragged*)c->ragged;
+  if (!r) return;
+  for (auto& kv : r->views) free_view(kv.second);
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  release_buffers(r);
+  delete r;
+  c->ragged = nullptr;
+}
+
+}  // namespace lisa
+
+using namespace lisa;
+
+extern "C" {
+
+int lisa_td_ragged_graph(lisa_td_ctx* c, int32_t enable) {
+  if (!c) return report_error(LISA_TD_EINVAL, "NULL context");
+  Ragged* r = state(c);
+  r->graph_on = enable ? 1 : 0;
+  return LISA_TD_OK;
+}
+
+int lisa_td_loglike_ragged(lisa_td_ctx* c, const double* params_dev, int32_t W,
+                           const int64_t* n_host, double* logl_dev, int32_t* status_dev,
+                           void* stream) {
+  if (!c || !params_dev || !n_host || !logl_dev) return report_error(LISA_TD_EINVAL, "NULL argument");
+  if (W < 1) return report_error(LISA_TD_EINVAL, "W must be >= 1");
+  if (W > c->cfg.max_walkers) return report_error(LISA_TD_ERANGE, "W=%d above max_walkers=%d", W, c->cfg.max_walkers);
+  if (!c->has_data) return report_error(LISA_TD_EINVAL, "lisa_td_set_data has not been called");
+  if (c->n % kTdiTile) return report_error(LISA_TD_EINVAL, "ragged batches need n to be a multiple of %d", kTdiTile);
+  // classes: window length -> walkers (in input order)
+  std::map<int64_t, std::vector<int32_t>> cls;
+  for (int w = 0; w < W; ++w) {
+    const int64_t nv = n_host[w];
+    FftPlan p;
+    if (nv < 2 * kTdiTile || nv > c->n || nv % kTdiTile || plan_fft(nv, &p) != 0)
+      return report_error(LISA_TD_EINVAL,
+                          "n[%d]=%lld: window lengths must be multiples of %d, 2^a 3^b 5^c 7^d, "
+                          "in [%d, n]", w, (long long)nv, kTdiTile, 2 * kTdiTile);
+    cls[nv].push_back(w);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  Ragged* r = state(c);
+  cudaError_t e = ensure_buffers(r, W);
+  if (e != cudaSuccess) return report_error(LISA_TD_ENOMEM, "ragged buffers: %s", cudaGetErrorString(e));
+  // the ring entry's previous upload must have completed before it is rewritten
+  r->ring ^= 1;
+  r->perm_host = r->perm_ring[r->ring];
+  e = cudaEventSynchronize(r->perm_ev[r->ring]);
+  if (e != cudaSuccess) return report_error(LISA_TD_ECUDA, "ragged: %s", cudaGetErrorString(e));
+  std::vector<View*> views;
+  std::vector<int64_t> key;
+  int k = 0;
+  for (auto& kv : cls) {
+    View* vw = nullptr;
+    e = get_view(c, r, kv.first, s, &vw);
+    if (e != cudaSuccess) return report_error(LISA_TD_ECUDA, "ragged view n=%lld: %s", (long long)kv.first, cudaGetErrorString(e));
+    views.push_back(vw);
+    key.push_back(kv.first);
+    key.push_back((int64_t)kv.second.size());
+    for (int32_t w : kv.second) r->perm_host[k++] = w;
+  }
+  key.push_back((int64_t)(uintptr_t)params_dev);
+  key.push_back((int64_t)(uintptr_t)logl_dev);
+  key.push_back((int64_t)(uintptr_t)status_dev);
+  e = cudaMemcpyAsync(r->perm_dev, r->perm_host, sizeof(int32_t) * W, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventRecord(r->perm_ev[r->ring], s);
+  if (e != cudaSuccess) return report_error(LISA_TD_ECUDA, "ragged: %s", cudaGetErrorString(e));
+
+  auto enqueue = [&]() -> cudaError_t {
+    int start = 0, ci = 0;
+    for (auto& kv : cls) {
+      const int Wc = (int)kv.second.size();
+      View* vw = views[ci++];
+      gather_kernel<<<(unsigned)((Wc * 15 + 255) / 256), 256, 0, s>>>(params_dev, r->perm_dev,
+                                                                     start, Wc, r->params_ws);
+      cudaError_t er = cudaGetLastError();
+      if (er != cudaSuccess) return er;
+      er = run_loglike_stages(&vw->v, r->params_ws, Wc, r->logl_ws, r->status_ws, s, nullptr);
+      if (er != cudaSuccess) return er;
+      scatter_kernel<<<(unsigned)((Wc + 127) / 128), 128, 0, s>>>(r->logl_ws, r->status_ws,
+                                                                  r->perm_dev, start, Wc, logl_dev,
+                                                                  status_dev);
+      er = cudaGetLastError();
+      if (er != cudaSuccess) return er;
+      start += Wc;
+    }
+    return cudaSuccess;
+  };
+
+  if (!r->graph_on || s == nullptr) {
+    e = enqueue();
+    return e == cudaSuccess ? LISA_TD_OK : report_error(LISA_TD_ECUDA, "ragged: %s", cudaGetErrorString(e));
+  }
+  if (!r->exec || key != r->key) {
+    if (r->exec) {
+      cudaGraphExecDestroy(r->exec);
+      r->exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t eq = enqueue();
+      e = cudaStreamEndCapture(s, &g);
+      if (eq != cudaSuccess) e = eq;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&r->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      r->exec = nullptr;
+      return report_error(LISA_TD_ECUDA, "ragged graph capture: %s", cudaGetErrorString(e));
+    }
+    r->key = key;
+  }
+  e = cudaGraphLaunch(r->exec, s);
+  return e == cudaSuccess ? LISA_TD_OK : report_error(LISA_TD_ECUDA, "ragged graph launch: %s", cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -102,6 +102,45 @@ def prior_draws(w, n, dt, seed, precessing=False, tc_frac=(0.90, 0.98),
     return out
 
 
+# window lengths of the ragged workload: whole days k with k 7-smooth, so that
+# n_w = 17280 k is a multiple of 64 and an FFT length of radices 2, 3, 5, 7
+def _smooth(k):
+    for p in (2, 3, 5, 7):
+        while k % p == 0:
+            k //= p
+    return k == 1
+
+
+RAGGED_DAYS = tuple(k for k in range(1, 61) if _smooth(k))
+
+
+def newtonian_time_to_merger(m1, m2, f):
+    """Newtonian (2,2) time from gravitational-wave frequency f to merger [s]."""
+    mt = (m1 + m2) * 4.925490947641267e-06
+    mc = mt * (m1 * m2 / (m1 + m2) ** 2) ** 0.6
+    return 5.0 / 256.0 * (math.pi * f) ** (-8.0 / 3.0) * mc ** (-5.0 / 3.0)
+
+
+def ragged_walkers(w, n, dt, seed, precessing=True, f_min=1e-4, pad_s=2 * DAY):
+    """Walkers of uneven signal length on an n-sample grid: prior draws whose
+    window T_w = clamp(time to merger from f_min + pad, 1 d, n dt) is rounded up
+    to a whole number of days k with k in RAGGED_DAYS; the merger sits at
+    t_c = t_end - U(0.02, 0.10) T_w inside the window.  -> (params, n_w)."""
+    rng = np.random.default_rng(seed + 7)
+    th = prior_draws(w, n, dt, seed, precessing=precessing)
+    days_max = n * dt / DAY
+    nw = np.empty(w, dtype=np.int64)
+    for k in range(w):
+        tau = newtonian_time_to_merger(th[k, 0], th[k, 1], f_min) + pad_s
+        d = min(max(tau / DAY, 1.0), days_max)
+        kd = next((q for q in RAGGED_DAYS if q >= d - 1e-9 and q <= days_max), None)
+        if kd is None:
+            kd = max(q for q in RAGGED_DAYS if q <= days_max)
+        nw[k] = int(round(kd * DAY / dt))
+        th[k, 14] = n * dt - rng.uniform(0.02, 0.10) * nw[k] * dt
+    return th, nw
+
+
 def table1_precessing(n, dt, tc_frac=0.9):
     """The injection of Table I (precessing columns), t_c at a fraction of the window."""
     r = math.radians
