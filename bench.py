@@ -37,8 +37,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5
 # capture of 30 d x 64 walkers (profiles/tdi_mixed_kernel_30d_64w.md,
 # profiles/project_mixed_kernel_30d_64w.md); traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
-NCU_BYTES_PER_UNIT = {"tdi": 1222.564608e6 / (518400 * 64),
-                      "project": 1218.176512e6 / (518400 * 64)}
+NCU_BYTES_PER_UNIT = {"tdi": None, "project": None}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -192,6 +191,56 @@ def _inject(torch, api, lk_ref, lk_all, params, n, snr=2000.0):
     return aet, rho
 
 
+def ragged_measure(torch, api, workloads, dev, steps, W=256):
+    """Walkers of uneven duration (1-60 d windows set by the time to merger of
+    their masses), precessing, five modes, Keplerian, TDI 2: one
+    lisa_td_loglike_ragged per step, replayed as a CUDA graph; mixed and FP64
+    paths on the same walkers, and |dlogL| on walkers near the injection."""
+    import numpy as np
+    cfg = workloads.config("c3_prec_60d")
+    kw = _gpu_kwargs(cfg)
+    th, nw = workloads.ragged_walkers(W, cfg["n"], cfg["dt"], seed=4)
+    lk32 = api.Likelihood(precision=1, max_walkers=W, **kw)
+    lk64 = api.Likelihood(precision=0, max_walkers=W, **kw)
+    params = torch.as_tensor(th, device=dev)
+    _inject(torch, api, lk64, [lk32, lk64], params, cfg["n"])
+    nw[1:8] = nw[0]                                    # bulk walkers share walker 0's window
+    stream = torch.cuda.Stream()
+    logl = torch.empty(W, dtype=torch.float64, device=dev)
+    api.lisa_td_ragged_graph(lk32.ctx, 1)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            api.lisa_td_loglike_ragged(lk32.ctx, params, W, nw, logl, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            api.lisa_td_loglike_ragged(lk32.ctx, params, W, nw, logl, None, stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    l32 = logl.clone()
+    with torch.cuda.stream(stream):
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        api.lisa_td_loglike_ragged(lk64.ctx, params, W, nw, logl, None, stream)
+        f1.record(stream)
+    stream.synchronize()
+    ms64 = f0.elapsed_time(f1)
+    d = (l32 - logl).abs().cpu().numpy()
+    days = nw / (86400.0 / cfg["dt"])
+    lk32.close()
+    lk64.close()
+    return {"workload": "c3_prec_60d: 256 precessing walkers, windows 1-60 d from the time to "
+                        "merger (whole 7-smooth days), 5 mode pairs, Keplerian, TDI 2, p = 31",
+            "value": round(W * steps / (ms32 * 1e-3), 2), "unit": "logL evals/s",
+            "ms_per_step": round(ms32 / steps, 3), "steps": steps,
+            "fp64_value": round(W / (ms64 * 1e-3), 3),
+            "classes": int(len(np.unique(nw))),
+            "window_days": [float(days.min()), float(np.median(days)), float(days.max())],
+            "walker_samples_per_step": int(nw.sum()),
+            "max_abs_dlogL_bulk": float(d[:8].max()), "graph": True}
+
+
 def run_ours(args):
     ws, rank, lrank = _dist()
     torch, api, workloads = _setup_gpu(lrank)
@@ -314,6 +363,8 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, theta[0], aet.cpu().numpy())
+    if not args.no_ragged:
+        out["ragged"] = ragged_measure(torch, api, workloads, dev, max(2, args.steps // 2))
     if not args.no_proposals:
         # learned proposal vs the Fisher-Gaussian one, on the exact likelihood
         from paper_2501_08261_gb300 import proposals
@@ -378,6 +429,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-proposals", action="store_true",
                     help="skip the flow vs Fisher-Gaussian proposal measurement")
+    ap.add_argument("--no-ragged", action="store_true",
+                    help="skip the uneven-duration (ragged) batch measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

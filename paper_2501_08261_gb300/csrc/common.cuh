@@ -61,6 +61,8 @@ struct MixMode {
   float ph0;           // m phi_m reduced to (-pi, pi]
   float yp_re, yp_im, ym_re, ym_im;
   int l, m;
+  float yc[2][3];      // precessing: coefficients of the D-matrix sum for +m (0) and -m (1),
+                       // terms r = max(+-m - 2, 0) + q, prefactor included (zero past the end)
 };
 struct MixRec {
   df32 T;              // t_c - t0

@@ -188,6 +188,19 @@ __global__ void prep_kernel(const double* __restrict__ params, int W, int Wpad, 
     Q.ym_im = (float)Md.Ym_im;
     Q.l = Md.l;
     Q.m = Md.m;
+    for (int sg = 0; sg < 2; ++sg) {
+      const int l = Md.l, mm = sg ? -Md.m : Md.m;
+      const int r0 = mm - 2 > 0 ? mm - 2 : 0;
+      const int r1 = (l + mm < l - 2) ? l + mm : l - 2;
+      const double pref = sqrt(fact(l + 2) * fact(l - 2) / (fact(l + mm) * fact(l - mm))) *
+                          sqrt((2.0 * l + 1.0) / (4.0 * kPi));
+      for (int q = 0; q < 3; ++q) {
+        const int r = r0 + q;
+        Q.yc[sg][q] = r <= r1 ? (float)(binom(l + mm, r) * binom(l - mm, l - 2 - r) *
+                                         ((r & 1) ? -1.0 : 1.0) * pref)
+                              : 0.0f;
+      }
+    }
   }
   out[w] = R;
 }

@@ -125,13 +125,13 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
     int tile, int halo, int nL, float rL) {
-  // shared memory: h+ and hx planes [rows][32] (walker = bank: conflict-free
-  // whatever each walker's stencil row), then the tile's orbit records
-  extern __shared__ float smf[];
+  // shared memory: (h+, hx) pairs [rows][32] -- 256-byte rows, so that a
+  // 64-bit load of lane w touches banks 2w, 2w+1 whatever row each walker's
+  // stencil is on (conflict-free per half-warp) -- then the orbit records
+  extern __shared__ float2 smf2[];
   const int rows = tile + 2 * halo;
-  float* hps = smf;
-  float* hcs = smf + rows * 32;
-  OrbitRec32* ors = reinterpret_cast<OrbitRec32*>(smf + 2 * rows * 32);
+  float2* hws = smf2;
+  OrbitRec32* ors = reinterpret_cast<OrbitRec32*>(smf2 + rows * 32);
   __shared__ int shift_s[32];
   __shared__ float fra_s[32], p1_s[32], sa_s[32];
   __shared__ float cinv_s[K];
@@ -165,9 +165,7 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     const float2* hw = h + (int64_t)w * n;
     for (int r = warp; r < rows; r += nw) {
       int64_t g = a0w + r;
-      float2 v = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
-      hps[r * 32 + lane] = v.x;
-      hcs[r * 32 + lane] = v.y;
+      hws[r * 32 + lane] = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
     }
   }
   __syncthreads();
@@ -194,8 +192,9 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     if (loc >= 0 && loc + K <= rows) {
 #pragma unroll
       for (int j = 0; j < K; ++j) {
-        sp = fmaf(wts[j], hps[(loc + j) * 32 + lane], sp);
-        sc = fmaf(wts[j], hcs[(loc + j) * 32 + lane], sc);
+        const float2 v = hws[(loc + j) * 32 + lane];
+        sp = fmaf(wts[j], v.x, sp);
+        sc = fmaf(wts[j], v.y, sc);
       }
     } else {
       for (int j = 0; j < K; ++j) {
@@ -259,7 +258,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
                                                      c->orb64, (const double2*)h, (double*)y,
                                                      tile, halo);
   } else {
-    size_t smem = (size_t)2 * (tile + 2 * halo) * 32 * sizeof(float) +
+    size_t smem = (size_t)(tile + 2 * halo) * 32 * sizeof(float2) +
                   (size_t)tile * sizeof(OrbitRec32);
     double q = kArmSec / dt;
     int nL = (int)floor(q);

@@ -269,6 +269,18 @@ constexpr int kMixWarps = kMixTile / kMixSpt;
 constexpr int kPW2 = 33;                    // padded walker pairs per row
 
 struct f2 { float x, y; };                  // two walkers of one lane
+
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ f2 ld2(const float2* p) { float2 v = *p; return {v.x, v.y}; }
 
 // compensated (Knuth two-sum) accumulation of the |y|-sized centre samples:
@@ -382,8 +394,9 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
   constexpr int SPT = kMixSpt;
   extern __shared__ float2 smem2[];
   const int rows = kMixTile + hl + hr;
-  float2* yw = smem2;                              // [rows][kPW2]
-  float2* dyw = smem2 + rows * kPW2;               // dy_r = y_{r+1} - y_r
+  float2* ybuf0 = smem2;                           // [rows][kPW2], links 0, 2, 4
+  float2* ybuf1 = smem2 + rows * kPW2;             // links 1, 3, 5
+  float2* dyw = smem2 + 2 * rows * kPW2;           // dy_r = y_{r+1} - y_r of the current link
   __shared__ TdiTileTerm tts[42];
   const int lane = threadIdx.x, warp = threadIdx.y;
   const int tid = warp * 32 + lane;
@@ -402,17 +415,27 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
   for (int r = 0; r < SPT; ++r)
     mx[r] = my[r] = mz[r] = sx[r] = sy[r] = sz[r] = f2{0.0f, 0.0f};
 
-  for (int j = 0; j < kNLink; ++j) {
-    __syncthreads();
+  // y rows of link j -> dst by asynchronous copies (zeros outside the grid and
+  // for walkers >= W), so that the next link's loads overlap this link's FIRs
+  auto stage = [&](int j, float2* dst) {
     for (int r = warp; r < rows; r += kMixWarps) {
-      int64_t g = i0 - hl + r;
-      float2 v = make_float2(0.0f, 0.0f);
-      if (g >= 0 && g < n) {
-        const float* src = y + ((int64_t)j * n + g) * ldw;
-        if (wa < W) v.x = src[wa];
-        if (wa + 1 < W) v.y = src[wa + 1];
-      }
-      yw[r * kPW2 + lane] = v;
+      const int64_t g = i0 - hl + r;
+      float* d = reinterpret_cast<float*>(dst + r * kPW2 + lane);
+      const bool in = g >= 0 && g < n;
+      const float* src = in ? y + ((int64_t)j * n + g) * ldw + wa : y;
+      if (in && wa < W) cp_async4(d, src); else d[0] = 0.0f;
+      if (in && wa + 1 < W) cp_async4(d + 1, src + 1); else d[1] = 0.0f;
+    }
+    cp_async_commit();
+  };
+  stage(0, ybuf0);
+  for (int j = 0; j < kNLink; ++j) {
+    float2* yw = (j & 1) ? ybuf1 : ybuf0;
+    if (j + 1 < kNLink) {
+      stage(j + 1, (j & 1) ? ybuf0 : ybuf1);      // its buffer was last read by link j - 1
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
     for (int r = warp; r < rows; r += kMixWarps) {
@@ -462,6 +485,7 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
         }
       }
     }
+    __syncthreads();                               // link j's buffers are free again
   }
   const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f, r3 = 0.57735026918962576f;
 #pragma unroll
@@ -517,7 +541,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
   } else {
     int hlm = (int)ceil(nd * 1.1 * kArmSec / dt) + K / 2 + 3;
     int hrm = K / 2 + 2;
-    size_t smem = (size_t)2 * (kMixTile + hlm + hrm) * kPW2 * sizeof(float2);
+    size_t smem = (size_t)3 * (kMixTile + hlm + hrm) * kPW2 * sizeof(float2);
     dim3 gridm((unsigned)((c->n + kMixTile - 1) / kMixTile), (unsigned)((W + 63) / 64));
     cudaFuncSetAttribute(tdi_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);

@@ -90,6 +90,62 @@ __global__ void waveform_fp64_kernel(const WalkerRec* __restrict__ walkers, int6
 // phase of a months-long signal keeps ~1e-7 rad), reduced mod 2 pi, then FP32.
 // ---------------------------------------------------------------------------
 
+// Powers of the quaternion's complex components Qa = q0 + i q3, Qb = q2 + i q1
+// and of their conjugates, as far as the D-matrix sum of l <= 4, |m| <= 4
+// reaches (Qa^8, Qb^8, conj^2), built once per sample by repeated products.
+struct QPow {
+  float ar[9], ai[9], br[9], bi[9], cr[3], ci[3], dr[3], di[3];
+};
+
+__device__ inline void qpow_fill(const float* q, QPow& P) {
+  P.ar[0] = 1.0f; P.ai[0] = 0.0f; P.br[0] = 1.0f; P.bi[0] = 0.0f;
+  P.cr[0] = 1.0f; P.ci[0] = 0.0f; P.dr[0] = 1.0f; P.di[0] = 0.0f;
+#pragma unroll
+  for (int k = 1; k < 9; ++k) {
+    P.ar[k] = P.ar[k - 1] * q[0] - P.ai[k - 1] * q[3];
+    P.ai[k] = P.ar[k - 1] * q[3] + P.ai[k - 1] * q[0];
+    P.br[k] = P.br[k - 1] * q[2] - P.bi[k - 1] * q[1];
+    P.bi[k] = P.br[k - 1] * q[1] + P.bi[k - 1] * q[2];
+  }
+#pragma unroll
+  for (int k = 1; k < 3; ++k) {
+    P.cr[k] = P.cr[k - 1] * q[0] + P.ci[k - 1] * q[3];      // conj(Qa)^k
+    P.ci[k] = -P.cr[k - 1] * q[3] + P.ci[k - 1] * q[0];
+    P.dr[k] = P.dr[k - 1] * q[2] + P.di[k - 1] * q[1];      // conj(Qb)^k
+    P.di[k] = -P.dr[k - 1] * q[1] + P.di[k - 1] * q[2];
+  }
+}
+
+// sqrt((2l+1)/4pi) D^l_{M,2} from the power table: sum over r of
+// c_r Qa^(L+M-r) conj(Qa)^(L-2-r) Qb^(2-M+r) conj(Qb)^r (ylm_from_quat's sum
+// with compile-time exponents; coefficients c_r from the walker record)
+template <int L, int M>
+__device__ inline void ylm_pow(const QPow& P, const float* c, float& re, float& im) {
+  constexpr int r0 = M - 2 > 0 ? M - 2 : 0;
+  constexpr int r1 = (L + M < L - 2) ? L + M : L - 2;
+  re = 0.0f;
+  im = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int r = r0 + q;
+    if (r <= r1) {
+      const float xr = P.ar[L + M - r] * P.cr[L - 2 - r] - P.ai[L + M - r] * P.ci[L - 2 - r];
+      const float xi = P.ar[L + M - r] * P.ci[L - 2 - r] + P.ai[L + M - r] * P.cr[L - 2 - r];
+      const float yr = P.br[2 - M + r] * P.dr[r] - P.bi[2 - M + r] * P.di[r];
+      const float yi = P.br[2 - M + r] * P.di[r] + P.bi[2 - M + r] * P.dr[r];
+      re = fmaf(c[q], xr * yr - xi * yi, re);
+      im = fmaf(c[q], xr * yi + xi * yr, im);
+    }
+  }
+}
+
+template <int L, int M>
+__device__ inline void ylm_pair(const QPow& P, const MixMode& Md, float& ypr, float& ypi,
+                                float& ymr, float& ymi) {
+  ylm_pow<L, M>(P, Md.yc[0], ypr, ypi);
+  ylm_pow<L, -M>(P, Md.yc[1], ymr, ymi);
+}
+
 __device__ inline float planck_up_f(float x, float T) {      // x = t - t_a
   if (x <= 0.0f) return 0.0f;
   if (x >= T) return 1.0f;
@@ -143,6 +199,7 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
   float v = insp ? cbrtf(Mw) : 0.0f;
   float v2 = v * v;
   float qT[4];
+  QPow P;
   if (precessing) {
     // a = 2 nu u + S cos(th1) and G(a) - G_ref in double-float: alpha_c can
     // reach ~400 for q = 8, so G needs more than FP32's 24 bits
@@ -178,6 +235,7 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
     qT[1] = q1[0] * b[1] + q1[1] * b[0] + q1[2] * b[3] - q1[3] * b[2];
     qT[2] = q1[0] * b[2] - q1[1] * b[3] + q1[2] * b[0] + q1[3] * b[1];
     qT[3] = q1[0] * b[3] + q1[1] * b[2] - q1[2] * b[1] + q1[3] * b[0];
+    qpow_fill(qT, P);
   }
   // powers e^{-i m phi}, m = 1..4
   float pr[5], pi_[5];
@@ -195,8 +253,14 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
       float vp = Md.pw == 0 ? v2 : (Md.pw == 1 ? v2 * v : v2 * v2);
       amp = Md.pref * vp;
       freq = (float)Md.m * Mw * X.invM;
-      hr = pr[Md.m];
-      hi = pi_[Md.m];
+      hr = pr[1];
+      hi = pi_[1];
+#pragma unroll
+      for (int k = 2; k <= 4; ++k)                 // register select of e^{-i m phi}
+        if (k == Md.m) {
+          hr = pr[k];
+          hi = pi_[k];
+        }
     } else {
       amp = Md.A_m * (1.0f + Md.a_lm * tau) * dec;
       float ph = Md.ph0 + Md.w_rd * tau + Md.dw * X.tau_d * (1.0f - dec);
@@ -212,9 +276,12 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
     float sg = (Md.l & 1) ? -1.0f : 1.0f;
     float ypr, ypi, ymr, ymi;
     if (precessing) {
-      cplx<float> a = ylm_from_quat<float>(Md.l, Md.m, qT);
-      cplx<float> b = ylm_from_quat<float>(Md.l, -Md.m, qT);
-      ypr = a.re; ypi = a.im; ymr = b.re; ymi = b.im;
+      const int lm = Md.l * 8 + Md.m;
+      if (lm == 2 * 8 + 2) ylm_pair<2, 2>(P, Md, ypr, ypi, ymr, ymi);
+      else if (lm == 2 * 8 + 1) ylm_pair<2, 1>(P, Md, ypr, ypi, ymr, ymi);
+      else if (lm == 3 * 8 + 3) ylm_pair<3, 3>(P, Md, ypr, ypi, ymr, ymi);
+      else if (lm == 3 * 8 + 2) ylm_pair<3, 2>(P, Md, ypr, ypi, ymr, ymi);
+      else ylm_pair<4, 4>(P, Md, ypr, ypi, ymr, ymi);
     } else {
       ypr = Md.yp_re; ypi = Md.yp_im; ymr = Md.ym_re; ymi = Md.ym_im;
     }
