@@ -178,6 +178,8 @@ __device__ C* transform(C* buf0, C* buf1, int m, int P, const Radices& rd,
   return A;
 }
 
+constexpr int kU = 8;   // global loads batched per thread in the staging loops
+
 template <typename R>
 __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
                                                     typename CT<R>::T* __restrict__ fy, int64_t n,
@@ -196,17 +198,42 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
   const int c = chans[blockIdx.z];
   const int Wpad = 2 * Pt;
   const C* xc = reinterpret_cast<const C*>(x + (int64_t)c * n * Wpad);
-  for (int item = threadIdx.x; item < n1 * Pb; item += blockDim.x) {
-    const int a = item / Pb, p = item % Pb;
-    b0[item] = xc[((int64_t)n2 * a + b) * Pt + pb0 + p];
+  // staging: kU independent loads in flight per thread before the stores
+  const int total = n1 * Pb;
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kU) {
+    C v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) {
+        const int a = item / Pb, p = item % Pb;
+        v[u] = xc[((int64_t)n2 * a + b) * Pt + pb0 + p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) b0[item] = v[u];
+    }
   }
   __syncthreads();
   C* res = transform(b0, b1, n1, Pb, rd, (const C*)tws);
   C* out = fy + (int64_t)c * n * Pt;
-  for (int item = threadIdx.x; item < n1 * Pb; item += blockDim.x) {
-    const int k1 = item / Pb, p = item % Pb;
-    C v = cmulv(res[item], twn[(int64_t)b * k1]);
-    out[((int64_t)k1 * n2 + b) * Pt + pb0 + p] = v;
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kU) {
+    C t[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) t[u] = twn[(int64_t)b * (item / Pb)];
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) {
+        const int k1 = item / Pb, p = item % Pb;
+        out[((int64_t)k1 * n2 + b) * Pt + pb0 + p] = cmulv(res[item], t[u]);
+      }
+    }
   }
 }
 
@@ -219,11 +246,12 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
                                                     const int* __restrict__ chans) {
   using C = typename CT<R>::T;
   extern __shared__ unsigned char smem_raw[];
-  C* a0 = reinterpret_cast<C*>(smem_raw);
-  C* a1 = a0 + (size_t)n2 * Pb;
-  C* c0 = a1 + (size_t)n2 * Pb;
-  C* c1 = c0 + (size_t)n2 * Pb;
-  C* tws = c1 + (size_t)n2 * Pb;                   // W_n2^j, j < n2
+  // rows rA and rB side by side: columns [0, Pb) of row rA, [Pb, 2 Pb) of row
+  // rB, transformed together (one set of radix stages for both)
+  const int P2 = 2 * Pb;
+  C* u0 = reinterpret_cast<C*>(smem_raw);          // [n2][2 Pb]
+  C* u1 = u0 + (size_t)n2 * P2;
+  C* tws = u1 + (size_t)n2 * P2;                   // W_n2^j, j < n2
   for (int j = threadIdx.x; j < n2; j += blockDim.x) tws[j] = tw2[j];
   __shared__ double red[512];
   const int rp = blockIdx.x;
@@ -232,14 +260,30 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   const int rA = rp, rB = (n1 - rp) % n1;
   const bool single = (rA == rB);
   const C* in = fy + (int64_t)c * n * Pt;
-  for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
-    const int j = item / Pb, p = item % Pb;
-    a0[item] = in[((int64_t)rA * n2 + j) * Pt + pb0 + p];
-    if (!single) c0[item] = in[((int64_t)rB * n2 + j) * Pt + pb0 + p];
+  const int total = n2 * Pb;
+  for (int base = threadIdx.x; base < total; base += blockDim.x * kU) {
+    C va[kU], vc[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) {
+        const int j = item / Pb, p = item % Pb;
+        va[u] = in[((int64_t)rA * n2 + j) * Pt + pb0 + p];
+        vc[u] = in[((int64_t)rB * n2 + j) * Pt + pb0 + p];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int item = base + u * blockDim.x;
+      if (item < total) {
+        const int j = item / Pb, p = item % Pb;
+        u0[j * P2 + p] = va[u];
+        u0[j * P2 + Pb + p] = vc[u];
+      }
+    }
   }
   __syncthreads();
-  C* XA = transform(a0, a1, n2, Pb, rd, (const C*)tws);
-  C* XB = single ? XA : transform(c0, c1, n2, Pb, rd, (const C*)tws);
+  const C* X = transform(u0, u1, n2, P2, rd, (const C*)tws);
   const int64_t nb = n / 2 + 1;
   const double* wv = psdw + (c == 2 ? nb : 0);
   double accx = 0.0, accy = 0.0;     // walker 2p, 2p+1 (p fixed per thread); FP64: the
@@ -248,16 +292,16 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
     const int k2 = item / Pb, p = item % Pb;
     for (int rr = 0; rr < nrow; ++rr) {
-      const C* X = rr == 0 ? XA : XB;
-      const C* Xm = rr == 0 ? XB : XA;
+      const int co = rr == 0 ? 0 : Pb;             // this row's columns
+      const int cm = single ? 0 : Pb - co;         // its mirror row's columns
       const int row = rr == 0 ? rA : rB;
       const int64_t k = row + (int64_t)n1 * k2;
       if (k >= nb) continue;
       const double wk = wv[k];
       if (wk == 0.0) continue;
       const int km = (single && row == 0) ? (n2 - k2) % n2 : n2 - 1 - k2;
-      C z = X[k2 * Pb + p];
-      C zm = Xm[km * Pb + p];
+      C z = X[k2 * P2 + co + p];
+      C zm = X[km * P2 + cm + p];
       const double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
       const double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
       accx += wk * (xr * xr + xi * xi);

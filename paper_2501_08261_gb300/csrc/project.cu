@@ -190,12 +190,18 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     int loc = row0 + (int)fl - (K - 2) / 2;
     float sp = 0.0f, sc = 0.0f;
     if (loc >= 0 && loc + K <= rows) {
+      float sp1 = 0.0f, sc1 = 0.0f;                // two chains each (FMA latency)
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
+      for (int j = 0; j < K; j += 2) {
         const float2 v = hws[(loc + j) * 32 + lane];
+        const float2 u = hws[(loc + j + 1) * 32 + lane];
         sp = fmaf(wts[j], v.x, sp);
         sc = fmaf(wts[j], v.y, sc);
+        sp1 = fmaf(wts[j + 1], u.x, sp1);
+        sc1 = fmaf(wts[j + 1], u.y, sc1);
       }
+      sp += sp1;
+      sc += sc1;
     } else {
       for (int j = 0; j < K; ++j) {
         int64_t g = a0 + loc + j;
