@@ -201,8 +201,9 @@ def ragged_measure(torch, api, workloads, dev, steps, W=256):
     cfg = workloads.config("c3_prec_60d")
     kw = _gpu_kwargs(cfg)
     th, nw = workloads.ragged_walkers(W, cfg["n"], cfg["dt"], seed=4)
-    lk32 = api.Likelihood(precision=1, max_walkers=W, **kw)
-    lk64 = api.Likelihood(precision=0, max_walkers=W, **kw)
+    # room for one padding column per length class: the tiled ragged path
+    lk32 = api.Likelihood(precision=1, max_walkers=W + 64, **kw)
+    lk64 = api.Likelihood(precision=0, max_walkers=W + 64, **kw)
     params = torch.as_tensor(th, device=dev)
     _inject(torch, api, lk64, [lk32, lk64], params, cfg["n"])
     nw[1:8] = nw[0]                                    # bulk walkers share walker 0's window

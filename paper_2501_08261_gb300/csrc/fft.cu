@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
                                                     int n1, int n2, int Pt, int Pb, Radices rd,
                                                     const typename CT<R>::T* __restrict__ tw1,
                                                     const typename CT<R>::T* __restrict__ twn,
-                                                    const int* __restrict__ chans) {
+                                                    const int* __restrict__ chans,
+                                                    int64_t cstride, int ldc) {
   using C = typename CT<R>::T;
   extern __shared__ unsigned char smem_raw[];
   C* b0 = reinterpret_cast<C*>(smem_raw);
@@ -196,8 +197,8 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
   const int b = blockIdx.x;
   const int pb0 = blockIdx.y * Pb;
   const int c = chans[blockIdx.z];
-  const int Wpad = 2 * Pt;
-  const C* xc = reinterpret_cast<const C*>(x + (int64_t)c * n * Wpad);
+  // input rows of ldc complex values (walker pairs), channels cstride reals apart
+  const C* xc = reinterpret_cast<const C*>(x + (int64_t)c * cstride);
   // staging: kU independent loads in flight per thread before the stores
   const int total = n1 * Pb;
   for (int base = threadIdx.x; base < total; base += blockDim.x * kU) {
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
       const int item = base + u * blockDim.x;
       if (item < total) {
         const int a = item / Pb, p = item % Pb;
-        v[u] = xc[((int64_t)n2 * a + b) * Pt + pb0 + p];
+        v[u] = xc[((int64_t)n2 * a + b) * ldc + pb0 + p];
       }
     }
 #pragma unroll
@@ -377,8 +378,18 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
   const int* chans = c->chan_list;
   if (pass == 1) {
     dim3 g1((unsigned)p.n2, (unsigned)(Pt / pb1), (unsigned)nch);
-    pass1_kernel<R><<<g1, 512, sm1, s>>>((const R*)r, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
-                                         (const C*)p.tw1, (const C*)p.tw_n, chans);
+    // the input block: the whole [3][n][Wpad] buffer, or one length class's
+    // rows and columns inside a larger residual buffer (ragged batches)
+    const R* x = (const R*)r;
+    int64_t cstride = c->n * (int64_t)Wpad;
+    int ldc = Pt;
+    if (c->fft_ldr > 0) {
+      x += c->fft_roff * (int64_t)c->fft_ldr + c->fft_col0;
+      cstride = c->fft_cstride;
+      ldc = c->fft_ldr / 2;
+    }
+    pass1_kernel<R><<<g1, 512, sm1, s>>>(x, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
+                                         (const C*)p.tw1, (const C*)p.tw_n, chans, cstride, ldc);
   } else {
     dim3 g2((unsigned)(p.n1 / 2 + 1), (unsigned)(Pt / pb2), (unsigned)nch);
     pass2_kernel<R><<<g2, 512, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,

@@ -55,6 +55,17 @@ struct lisa_td_ctx {
   // bumped by lisa_td_set_data so that the views refresh their data windows
   void* ragged;
   int data_version;
+  // ragged batches on the common grid: woff[w] = first row of walker w's
+  // window (rows before it are outside the window: the waveform is not
+  // evaluated there and every stage reads them as zero); nullptr = row 0
+  const int64_t* woff;
+  // FFT input block of one length class: row offset, column offset and row
+  // stride (reals) inside the residual buffer, channel stride (reals);
+  // fft_ldr == 0 selects the whole buffer [3][n][Wpad]
+  int64_t fft_roff;
+  int fft_col0;
+  int fft_ldr;
+  int64_t fft_cstride;
 };
 
 namespace lisa {

@@ -22,8 +22,8 @@ __device__ void mode_coeff(int j, double nu, double delta, int& l, int& m, doubl
 }
 
 __global__ void prep_kernel(const double* __restrict__ params, int W, int Wpad, double t0,
-                            double dt, int mode_mask, int precessing,
-                            WalkerRec* __restrict__ out) {
+                            double dt, const int64_t* __restrict__ woff, int mode_mask,
+                            int precessing, WalkerRec* __restrict__ out) {
   int w = blockIdx.x * blockDim.x + threadIdx.x;
   if (w >= Wpad) return;
   int src_w = w < W ? w : 0;
@@ -69,7 +69,10 @@ __global__ void prep_kernel(const double* __restrict__ params, int W, int Wpad, 
   double us = pow(8.0 * kPi * R.M * kFmin, -1.0 / 3.0);
   double us2 = us * us, us4 = us2 * us2;
   R.t_start = R.tc - 5.0 * R.M * us4 * us4 / R.nu;
-  R.t_a = fmax(t0, R.t_start);
+  // the start taper begins at the later of the signal start and the start of
+  // the walker's window (the grid start, or its own window in ragged batches)
+  const double t0w = t0 + (woff ? (double)woff[w] * dt : 0.0);   // the window's first sample
+  R.t_a = fmax(t0w, R.t_start);
   insp_omega_phase(R, R.um, R.om_m, R.ph_m);
   double omdot = insp_omega_dot(R, R.um);
   double D = p[8] * kGpcSec;
@@ -128,14 +131,14 @@ __global__ void prep_kernel(const double* __restrict__ params, int W, int Wpad, 
 
   // ---- mixed-precision copy ----
   MixRec& X = R.mx;
-  X.T = df_from_double(R.tc - t0);
+  X.T = df_from_double(R.tc - t0w);
   X.kap = df_from_double(R.nu / (5.0 * R.M));
   X.A5 = df_from_double(1.0 / R.nu);
   X.A3 = df_from_double((5.0 / 3.0) * R.c1 / R.nu);
   X.A2 = df_from_double(2.5 * R.cs / R.nu);
-  X.tm = df_from_double(R.tm - t0);
-  X.tstart = df_from_double(R.t_start - t0);
-  X.ta = df_from_double(R.t_a - t0);
+  X.tm = df_from_double(R.tm - t0w);
+  X.tstart = df_from_double(R.t_start - t0w);
+  X.ta = df_from_double(R.t_a - t0w);
   X.dt = df_from_double(dt);
   X.c1 = (float)R.c1;
   X.cs = (float)R.cs;
@@ -211,7 +214,7 @@ cudaError_t launch_prep(const lisa_td_ctx* c, const double* params, int W, int W
                         cudaStream_t s) {
   int threads = 64;
   int blocks = (Wpad + threads - 1) / threads;
-  prep_kernel<<<blocks, threads, 0, s>>>(params, W, Wpad, c->cfg.t0, c->cfg.dt,
+  prep_kernel<<<blocks, threads, 0, s>>>(params, W, Wpad, c->cfg.t0, c->cfg.dt, c->woff,
                                          c->cfg.mode_mask, c->cfg.precessing, c->walkers);
   return cudaGetLastError();
 }

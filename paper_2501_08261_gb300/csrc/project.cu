@@ -19,11 +19,20 @@ namespace {
 
 constexpr int kPW = 33;                 // padded walkers per shared-memory row
 
+// every walker of the 32-walker group starts its window at or after row `end`
+// (walkers are sorted by window start, but take the minimum to be safe)
+__device__ inline bool tile_inactive(const int64_t* __restrict__ woff32, int64_t end) {
+  int64_t m = woff32[0];
+#pragma unroll 8
+  for (int k = 1; k < 32; ++k) m = woff32[k] < m ? woff32[k] : m;
+  return m >= end;
+}
+
 template <int K>
 __global__ void __launch_bounds__(128) project_fp64_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec64* __restrict__ orb, const double2* __restrict__ h, double* __restrict__ y,
-    int tile, int halo) {
+    int tile, int halo, const int64_t* __restrict__ woff) {
   extern __shared__ double2 win[];      // [(tile + 2 halo)][kPW]
   __shared__ int shift_s[32];
   __shared__ double cinv_s[K];
@@ -32,6 +41,8 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
   const int64_t i0 = (int64_t)blockIdx.x * tile;
   const int w = blockIdx.y * 32 + lane;
   const int rows = tile + 2 * halo;
+  if (woff && tile_inactive(woff + blockIdx.y * 32, i0 + tile)) return;
+  const int64_t lo = woff ? woff[w] : 0;        // this walker's window starts at row lo
   if (tid < K) cinv_s[tid] = lagrange_denom_inv<double, K>(tid);
   if (warp == 0) {
     const WalkerRec& R = walkers[w];
@@ -45,9 +56,10 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
   for (int ww = warp; ww < 32; ww += nw) {
     const int64_t a0 = i0 - shift_s[ww] - halo;
     const double2* hw = h + (int64_t)(blockIdx.y * 32 + ww) * n;
+    const int64_t lw = woff ? woff[blockIdx.y * 32 + ww] : 0;
     for (int r = lane; r < rows; r += 32) {
       int64_t g = a0 + r;
-      win[r * kPW + ww] = (g >= 0 && g < n) ? hw[g] : make_double2(0.0, 0.0);
+      win[r * kPW + ww] = (g >= lw && g >= 0 && g < n) ? hw[g] : make_double2(0.0, 0.0);
     }
   }
   __syncthreads();
@@ -59,12 +71,14 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
 #pragma unroll
   for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
 
+  // tau is relative to the window start lo (so that the fraction rounds as
+  // on a grid that starts there)
   auto interp = [&](double tau, double& hp, double& hc) {
     double fl = floor(tau);
     double eps = tau - fl;
     double wts[K];
     lagrange_weights<double, K>(eps, cinv, wts);
-    int64_t base = (int64_t)fl - (K - 2) / 2;
+    int64_t base = lo + (int64_t)fl - (K - 2) / 2;
     int64_t loc = base - a0;
     double sp = 0.0, sc = 0.0;
     if (loc >= 0 && loc + K <= rows) {
@@ -77,7 +91,7 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
     } else {                                   // outside the staged window: global reads
       for (int j = 0; j < K; ++j) {
         int64_t g = base + j;
-        if (g >= 0 && g < n) {
+        if (g >= lo && g >= 0 && g < n) {
           double2 v = hw[g];
           sp += wts[j] * v.x;
           sc += wts[j] * v.y;
@@ -96,21 +110,21 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       double kr = k0 * O.rr[q][0] + k1 * O.rr[q][1] + k2 * O.rr[q][2];
-      interp((double)i - kr / dt, hpr[q], hcr[q]);
+      interp((double)(i - lo) - kr / dt, hpr[q], hcr[q]);
     }
 #pragma unroll
     for (int j = 0; j < kNLink; ++j) {
       const int rq = link_receiver(j);
       double ks = k0 * O.rs[j][0] + k1 * O.rs[j][1] + k2 * O.rs[j][2];
       double hps, hcs;
-      interp((double)i - (O.L[j] + ks) / dt, hps, hcs);
+      interp((double)(i - lo) - (O.L[j] + ks) / dt, hps, hcs);
       double nx = O.n[j][0], ny = O.n[j][1], nz = O.n[j][2];
       double un = R.u[0] * nx + R.u[1] * ny + R.u[2] * nz;
       double vn = R.v[0] * nx + R.v[1] * ny + R.v[2] * nz;
       double kn = k0 * nx + k1 * ny + k2 * nz;
       double val = ((un * un - vn * vn) * (hps - hpr[rq]) + 2.0 * un * vn * (hcs - hcr[rq])) /
                    (2.0 * (1.0 - kn));
-      if (w < W) y[((int64_t)j * n + i) * ldw + w] = val;
+      if (w < W && i >= lo) y[((int64_t)j * n + i) * ldw + w] = val;
     }
   }
 }
@@ -124,7 +138,7 @@ template <int K>
 __global__ void __launch_bounds__(256) project_mixed_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
-    int tile, int halo, int nL, float rL) {
+    int tile, int halo, int nL, float rL, const int64_t* __restrict__ woff) {
   // shared memory: (h+, hx) pairs [rows][32] -- 256-byte rows, so that a
   // 64-bit load of lane w touches banks 2w, 2w+1 whatever row each walker's
   // stencil is on (conflict-free per half-warp) -- then the orbit records
@@ -139,6 +153,8 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
   const int tid = warp * 32 + lane, nth = 32 * nw;
   const int64_t i0 = (int64_t)blockIdx.x * tile;
   const int w = blockIdx.y * 32 + lane;
+  if (woff && tile_inactive(woff + blockIdx.y * 32, i0 + tile)) return;
+  const int64_t lo = woff ? woff[w] : 0;        // this walker's window starts at row lo
   if (tid < K) cinv_s[tid] = lagrange_denom_inv<float, K>(tid);
   if (warp == 0) {
     const WalkerRec& R = walkers[w];
@@ -165,7 +181,7 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     const float2* hw = h + (int64_t)w * n;
     for (int r = warp; r < rows; r += nw) {
       int64_t g = a0w + r;
-      hws[r * 32 + lane] = (g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
+      hws[r * 32 + lane] = (g >= lo && g >= 0 && g < n) ? hw[g] : make_float2(0.0f, 0.0f);
     }
   }
   __syncthreads();
@@ -205,7 +221,7 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     } else {
       for (int j = 0; j < K; ++j) {
         int64_t g = a0 + loc + j;
-        if (g >= 0 && g < n) {
+        if (g >= lo && g >= 0 && g < n) {
           float2 v = hw[g];
           sp = fmaf(wts[j], v.x, sp);
           sc = fmaf(wts[j], v.y, sc);
@@ -241,7 +257,7 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
       float kn = k0 * nx + k1 * ny + k2 * nz;
       float val = ((un * un - vn * vn) * (hps_ - hpr[rq]) + 2.0f * un * vn * (hcs_ - hcr[rq])) /
                   (2.0f * (1.0f - kn));
-      if (w < W) y[((int64_t)j * n + i) * ldw + w] = val;
+      if (w < W && i >= lo) y[((int64_t)j * n + i) * ldw + w] = val;
     }
   }
 }
@@ -262,7 +278,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
                          (int)smem);
     project_fp64_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                      c->orb64, (const double2*)h, (double*)y,
-                                                     tile, halo);
+                                                     tile, halo, c->woff);
   } else {
     size_t smem = (size_t)(tile + 2 * halo) * 32 * sizeof(float2) +
                   (size_t)tile * sizeof(OrbitRec32);
@@ -274,7 +290,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
     dim3 blockm(32, 8);
     project_mixed_kernel<K><<<grid, blockm, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                       c->orb32, (const float2*)h, (float*)y,
-                                                      tile, halo, nL, rL);
+                                                      tile, halo, nL, rL, c->woff);
   }
   return cudaGetLastError();
 }

@@ -70,12 +70,19 @@ namespace {
 
 constexpr int kPW = 33;
 
+// every walker of a group starts its window at or after row `end`
+__device__ inline bool group_inactive(const int64_t* __restrict__ wo, int cnt, int64_t end) {
+  int64_t m = wo[0];
+  for (int k = 1; k < cnt; ++k) m = wo[k] < m ? wo[k] : m;
+  return m >= end;
+}
+
 template <int K, int SPT>
 __global__ void __launch_bounds__(128) tdi_fp64_kernel(
     const TdiTable* __restrict__ tab, int W, int ldw_in, int ldw_out, int64_t n, double dt,
     const OrbitRec64* __restrict__ orb,
     const double* __restrict__ y, double* __restrict__ out, const double* __restrict__ data,
-    int resid, int hl, int hr) {
+    int resid, int hl, int hr, const int64_t* __restrict__ woff) {
   constexpr int NW = 4;
   constexpr int TILE = NW * SPT;
   extern __shared__ double ywin[];              // [(TILE + hl + hr)][kPW]
@@ -84,6 +91,8 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
   const int64_t i0 = (int64_t)blockIdx.x * TILE;
   const int w = blockIdx.y * 32 + lane;
   const int rows = TILE + hl + hr;
+  if (woff && group_inactive(woff + blockIdx.y * 32, 32, i0 + TILE)) return;
+  const int64_t lo = woff ? woff[w] : 0;        // rows before lo: outside the walker's window
   if (warp == 0 && lane < K) cinv_s[lane] = lagrange_denom_inv<double, K>(lane);
   double ax[SPT], ay[SPT], az[SPT];      // X, Y, Z accumulators
 #pragma unroll
@@ -98,7 +107,7 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
     for (int r = warp; r < rows; r += NW) {
       int64_t g = i0 - hl + r;
       double v = 0.0;
-      if (g >= 0 && g < n && w < W) v = y[((int64_t)j * n + g) * ldw_in + w];
+      if (g >= lo && g >= 0 && g < n && w < W) v = y[((int64_t)j * n + g) * ldw_in + w];
       ywin[r * kPW + lane] = v;
     }
     __syncthreads();
@@ -118,11 +127,11 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
           double D = 0.0;
 #pragma unroll
           for (int l = 0; l < kNLink; ++l) D += (double)T.cnt[l] * L[l];
-          double tau = (double)i - D / dt;
+          double tau = (double)(i - lo) - D / dt;    // relative to the window start
           double fl = floor(tau);
           double wts[K];
           lagrange_weights<double, K>(tau - fl, cinv, wts);
-          int64_t base = (int64_t)fl - (K - 2) / 2;
+          int64_t base = lo + (int64_t)fl - (K - 2) / 2;
           int64_t loc = base - (i0 - hl);
           v = 0.0;
           if (loc >= 0 && loc + K <= rows) {
@@ -131,7 +140,7 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
           } else {
             for (int m = 0; m < K; ++m) {
               int64_t g = base + m;
-              if (g >= 0 && g < n && w < W) v += wts[m] * y[((int64_t)j * n + g) * ldw_in + w];
+              if (g >= lo && g >= 0 && g < n && w < W) v += wts[m] * y[((int64_t)j * n + g) * ldw_in + w];
             }
           }
         }
@@ -148,7 +157,7 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
 #pragma unroll
   for (int s = 0; s < SPT; ++s) {
     const int64_t i = i0 + warp + s * NW;
-    if (i >= n) continue;
+    if (i >= n || i < lo) continue;
     double X = ax[s], Y = ay[s], Z = az[s];
     double A = (Z - X) * r2, E = (X - 2.0 * Y + Z) * r6, T = (X + Y + Z) * r3;
     if (resid) {
@@ -390,7 +399,8 @@ template <int K>
 __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
     const TdiTable* __restrict__ tab, const TdiTileTerm* __restrict__ tiles, int W, int ldw,
     int64_t n, const float* __restrict__ y, float* __restrict__ out,
-    const float* __restrict__ data, int resid, int hl, int hr) {
+    const float* __restrict__ data, int resid, int hl, int hr,
+    const int64_t* __restrict__ woff) {
   constexpr int SPT = kMixSpt;
   extern __shared__ float2 smem2[];
   const int rows = kMixTile + hl + hr;
@@ -404,6 +414,9 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
   const int wa = blockIdx.y * 64 + 2 * lane;       // walkers wa, wa + 1
   const int s0 = warp * SPT;
   const int nd = tab->n_dterms;
+  if (woff && group_inactive(woff + blockIdx.y * 64, 64, i0 + kMixTile)) return;
+  // rows before lo_a / lo_b are outside the windows of walkers wa / wa + 1
+  const int64_t lo_a = woff ? woff[wa] : 0, lo_b = woff ? woff[wa + 1] : 0;
   {
     const int* src = reinterpret_cast<const int*>(tiles + (int64_t)blockIdx.x * nd);
     int* dst = reinterpret_cast<int*>(tts);
@@ -423,8 +436,8 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
       float* d = reinterpret_cast<float*>(dst + r * kPW2 + lane);
       const bool in = g >= 0 && g < n;
       const float* src = in ? y + ((int64_t)j * n + g) * ldw + wa : y;
-      if (in && wa < W) cp_async4(d, src); else d[0] = 0.0f;
-      if (in && wa + 1 < W) cp_async4(d + 1, src + 1); else d[1] = 0.0f;
+      if (in && g >= lo_a && wa < W) cp_async4(d, src); else d[0] = 0.0f;
+      if (in && g >= lo_b && wa + 1 < W) cp_async4(d + 1, src + 1); else d[1] = 0.0f;
     }
     cp_async_commit();
   };
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
       const int w = wa + e;
-      if (w >= W) continue;
+      if (w >= W || i < (e ? lo_b : lo_a)) continue;
       const float Mx = e ? mx[r].y : mx[r].x, My = e ? my[r].y : my[r].x, Mz = e ? mz[r].y : mz[r].x;
       const float Sx = e ? sx[r].y : sx[r].x, Sy = e ? sy[r].y : sy[r].x, Sz = e ? sz[r].y : sz[r].x;
       // A, E, T from the main parts combined error-free first, the small parts after
@@ -537,7 +550,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
                          (int)smem);
     tdi_fp64_kernel<K, SPT><<<grid, block, smem, s>>>(
         c->tdi_tab, W, ldw, ldw, c->n, dt, c->orb64, (const double*)y, (double*)out, c->data64,
-        resid, hl, hr);
+        resid, hl, hr, c->woff);
   } else {
     int hlm = (int)ceil(nd * 1.1 * kArmSec / dt) + K / 2 + 3;
     int hrm = K / 2 + 2;
@@ -548,7 +561,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
     dim3 blockm(32, kMixTile / kMixSpt);
     tdi_mixed_kernel<K><<<gridm, blockm, smem, s>>>(c->tdi_tab, c->tdi_tiles, W, ldw, c->n,
                                                    (const float*)y, (float*)out, c->data32,
-                                                   resid, hlm, hrm);
+                                                   resid, hlm, hrm, c->woff);
   }
   return cudaGetLastError();
 }

@@ -72,10 +72,12 @@ __device__ void polar_fp64(const WalkerRec& W, double t, int precessing, double&
 }
 
 __global__ void waveform_fp64_kernel(const WalkerRec* __restrict__ walkers, int64_t n,
-                                     double t0, double dt, int precessing, double2* h) {
+                                     double t0, double dt, int precessing, double2* h,
+                                     const int64_t* __restrict__ woff) {
   int w = blockIdx.y;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (woff && i < woff[w]) return;             // before the walker's window: never read
   const WalkerRec& W = walkers[w];
   double re, im;
   polar_fp64(W, t0 + (double)i * dt, precessing, re, im);
@@ -291,13 +293,17 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
 }
 
 __global__ void __launch_bounds__(128) waveform_mixed_kernel(
-    const WalkerRec* __restrict__ walkers, int64_t n, int precessing, float2* __restrict__ h) {
+    const WalkerRec* __restrict__ walkers, int64_t n, int precessing, float2* __restrict__ h,
+    const int64_t* __restrict__ woff) {
   const int w = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int64_t lo = woff ? woff[w] : 0;
+  if (i < lo) return;                          // before the walker's window: never read
   const MixRec& X = walkers[w].mx;
   float re, im;
-  polar_mixed(X, walkers[w].status, i, precessing, re, im);
+  // the double-float time anchors are relative to the window start
+  polar_mixed(X, walkers[w].status, i - lo, precessing, re, im);
   float Hr = re * X.c2psi - im * X.s2psi;
   float Hi = re * X.s2psi + im * X.c2psi;
   h[(int64_t)w * n + i] = make_float2(Hr, -Hi);
@@ -309,9 +315,10 @@ cudaError_t launch_waveform(const lisa_td_ctx* c, int W, void* h, cudaStream_t s
   dim3 grid((unsigned)((c->n + 127) / 128), (unsigned)W);
   if (c->cfg.precision == 0) {
     waveform_fp64_kernel<<<grid, 128, 0, s>>>(c->walkers, c->n, c->cfg.t0, c->cfg.dt,
-                                              c->cfg.precessing, (double2*)h);
+                                              c->cfg.precessing, (double2*)h, c->woff);
   } else {
-    waveform_mixed_kernel<<<grid, 128, 0, s>>>(c->walkers, c->n, c->cfg.precessing, (float2*)h);
+    waveform_mixed_kernel<<<grid, 128, 0, s>>>(c->walkers, c->n, c->cfg.precessing, (float2*)h,
+                                               c->woff);
   }
   return cudaGetLastError();
 }

@@ -33,6 +33,16 @@ def _walkers(n, windows, seed, precessing):
     return th
 
 
+def _bar(want, dd, precision):
+    """|dlogL| bar between two evaluations of the same window.  logL =
+    -1/2 (r|r) with r = h - d, so a norm-relative error eps on the series moves
+    logL by up to eps ||r|| ||d|| = eps sqrt(2|logL| 2|logL_0|) (logL_0 =
+    -1/2 (d|d)); eps = 1e-10 for FP64 (the series tolerance of the FP64 tests),
+    1e-6 for two mixed evaluations; and never below the fixed floors."""
+    eps, floor, rel = (1e-10, 1e-6, 1e-10) if precision == 0 else (1e-6, 1e-3, 1e-6)
+    return max(floor, rel * abs(want), eps * np.sqrt(4.0 * abs(want) * abs(dd)))
+
+
 def _window_ctx(cfg, nw, precision, W, d):
     kw = gpu_kwargs(cfg)
     kw["n"] = nw
@@ -59,9 +69,11 @@ def test_ragged_equals_per_window_likelihood(name, precision):
         sel = np.nonzero(windows == nw)[0]
         wl = _window_ctx(cfg, int(nw), precision, len(sel), d)
         want = wl.loglike(_t(th[sel])).cpu().numpy()
+        far = th[sel].copy()
+        far[:, 8] = 1e30                                        # h -> 0: -1/2 (d|d)
+        dd = wl.loglike(_t(far)).cpu().numpy()
         for k, w in enumerate(sel):
-            tol = max(1e-6, 1e-10 * abs(want[k])) if precision == 0 else max(1e-3, 1e-6 * abs(want[k]))
-            assert abs(got[w] - want[k]) <= tol, (nw, w, got[w], want[k])
+            assert abs(got[w] - want[k]) <= _bar(want[k], dd[k], precision), (nw, w, got[w], want[k])
         wl.close()
     lk.close()
     ref.close()
@@ -80,7 +92,10 @@ def test_ragged_matches_oracle():
         off = cfg["n"] - windows[w]
         sw = oracle_setup(dict(cfg, n=int(windows[w]), t0=cfg["t0"] + off * cfg["dt"]))
         want = pipeline.loglike(th[w], sw, d[:, off:])
-        assert abs(got[w] - want) <= max(1e-6, 1e-10 * abs(want)), (w, got[w], want)
+        far = th[w].copy()
+        far[8] = 1e30
+        dd = pipeline.loglike(far, sw, d[:, off:])
+        assert abs(got[w] - want) <= _bar(want, dd, 0), (w, got[w], want)
     lk.close()
 
 
@@ -122,3 +137,29 @@ def test_graph_replay_and_recapture_and_errors():
             lk.loglike_ragged(_t(th), wb)
     lk.close()
     ref.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tiled_and_per_class_paths_agree(precision):
+    """32 walkers in three odd-sized classes: a context with room for the
+    padding columns runs the tiled path, one without falls back to per-class
+    launches; both give the per-window likelihood."""
+    cfg = workloads.config("c3_prec_1d", n=4 * DAY)
+    windows = np.array([4] * 11 + [2] * 11 + [1] * 10) * DAY
+    np.random.default_rng(3).shuffle(windows)
+    th = _walkers(cfg["n"], windows, 14, True)
+    ref = api.Likelihood(precision=0, max_walkers=32, **gpu_kwargs(cfg))
+    d = ref.tdi(ref.project(_t(th[:1])))[:, :, 0].contiguous()
+    tiled = api.Likelihood(precision=precision, max_walkers=64, **gpu_kwargs(cfg))
+    per_class = api.Likelihood(precision=precision, max_walkers=32, **gpu_kwargs(cfg))
+    tiled.set_data(d)
+    per_class.set_data(d)
+    a = tiled.loglike_ragged(_t(th), windows).cpu().numpy()
+    b = per_class.loglike_ragged(_t(th), windows).cpu().numpy()
+    far = th.copy()
+    far[:, 8] = 1e30
+    dd = per_class.loglike_ragged(_t(far), windows).cpu().numpy()
+    for w in range(len(th)):
+        assert abs(a[w] - b[w]) <= _bar(b[w], dd[w], precision), (w, a[w], b[w])
+    for lk in (ref, tiled, per_class):
+        lk.close()
