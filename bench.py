@@ -37,8 +37,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5
 # capture of 30 d x 64 walkers (profiles/tdi_mixed_kernel_30d_64w.md,
 # profiles/project_mixed_kernel_30d_64w.md); traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
-NCU_BYTES_PER_UNIT = {"tdi": 1220.925440e6 / (518400 * 64),
-                      "project": 1216.348672e6 / (518400 * 64)}
+NCU_BYTES_PER_UNIT = {"tdi": 1220.824320e6 / (518400 * 64),
+                      "project": 1216.307712e6 / (518400 * 64)}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -209,6 +209,7 @@ def ragged_measure(torch, api, workloads, dev, steps, W=256):
     nw[1:8] = nw[0]                                    # bulk walkers share walker 0's window
     stream = torch.cuda.Stream()
     logl = torch.empty(W, dtype=torch.float64, device=dev)
+    api.lisa_td_autotune(lk32.ctx, params, W, nw)      # incl. each window length's FFT
     api.lisa_td_ragged_graph(lk32.ctx, 1)
     with torch.cuda.stream(stream):
         for _ in range(3):
@@ -276,6 +277,8 @@ def run_ours(args):
     def step64():
         api.lisa_td_loglike_batch(lk64.ctx, params, W, logl, None, stream)
 
+    # launch shapes measured once for this workload (lisa_td_autotune)
+    tuned = api.lisa_td_autotune(lk32.ctx, params, W)
     for _ in range(args.warmup):
         step32()
     torch.cuda.synchronize()
@@ -358,6 +361,8 @@ def run_ours(args):
         "mixed_vs_fp64": cmp,
         "stage_ms": {k: round(v, 4) for k, v in per_call.items()},
         "gpu_launches": 7 * args.steps,
+        "autotune": {"project_tile": tuned[0], "project_warps": tuned[1], "fft_pass1_pb": tuned[2],
+                     "fft_pass2_pb": tuned[3]},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": round(evals * args.steps / (ms_e2e * 1e-3), 2), "unit": "logL evals/s",

@@ -15,7 +15,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
-           "lisa_td_loglike_ragged", "lisa_td_ragged_graph",
+           "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
            "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept",
            "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
@@ -50,6 +50,7 @@ def load_library(path=None):
         "lisa_td_loglike_batch": ([P, P, I32, P, P, P], ctypes.c_int),
         "lisa_td_loglike_ragged": ([P, P, I32, P, P, P, P], ctypes.c_int),
         "lisa_td_ragged_graph": ([P, I32], ctypes.c_int),
+        "lisa_td_autotune": ([P, P, I32, P, P, P], ctypes.c_int),
         "lisa_td_profile": ([P, I32], ctypes.c_int),
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
@@ -158,6 +159,20 @@ def lisa_td_loglike_ragged(ctx, params, W, n_per_walker, logl, status=None, stre
     _check(lib().lisa_td_loglike_ragged(ctx, _ptr(params), int(W),
                                         nh.ctypes.data_as(ctypes.c_void_p), _ptr(logl),
                                         _ptr(status), _stream(stream)), "lisa_td_loglike_ragged")
+
+
+def lisa_td_autotune(ctx, params, W, n_per_walker=None, stream=None):
+    """-> (tile, warps, pass-1 pb, pass-2 pb) chosen and kept by the context."""
+    import numpy as np
+    ch = (ctypes.c_int32 * 4)()
+    if n_per_walker is None:
+        nh = None
+    else:
+        nh_arr = np.ascontiguousarray(n_per_walker, dtype=np.int64)
+        nh = nh_arr.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().lisa_td_autotune(ctx, _ptr(params), int(W), nh, ch, _stream(stream)),
+           "lisa_td_autotune")
+    return tuple(ch)
 
 
 def lisa_td_ragged_graph(ctx, enable):

@@ -339,10 +339,16 @@ __global__ void reduce_kernel(const double* __restrict__ partial, int nrp, int W
 }
 
 int pick_pb(int m, int nbuf, size_t csize, int Pt) {
-  int pb = 16;
+  // pass 1 (two buffers) gathers strided rows: more, smaller blocks hide the
+  // latency better (measured by the autotuner); pass 2 keeps wide blocks
+  int pb = nbuf == 2 ? 4 : 16;
   auto bytes = [&](int q) { return ((size_t)nbuf * q + 1) * m * csize; };
   while (pb > 1 && (bytes(pb) > 200 * 1024 || Pt % pb != 0)) pb /= 2;
   return bytes(pb) > 200 * 1024 ? 0 : pb;
+}
+
+bool pb_fits(int m, int nbuf, size_t csize, int Pt, int pb) {
+  return pb >= 1 && Pt % pb == 0 && ((size_t)nbuf * pb + 1) * m * csize <= 200 * 1024;
 }
 
 void radices_of(int m, Radices* rd) {
@@ -370,6 +376,8 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
   for (int q = 0; q < p.nr2; ++q) r2.r[q] = p.r2[q];
   int pb1 = pick_pb(p.n1, 2, sizeof(C), Pt);
   int pb2 = pick_pb(p.n2, 4, sizeof(C), Pt);
+  if (c->tune_pb1 > 0 && pb_fits(p.n1, 2, sizeof(C), Pt, c->tune_pb1)) pb1 = c->tune_pb1;
+  if (c->tune_pb2 > 0 && pb_fits(p.n2, 4, sizeof(C), Pt, c->tune_pb2)) pb2 = c->tune_pb2;
   if (pb1 == 0 || pb2 == 0) return cudaErrorInvalidValue;
   size_t sm1 = ((size_t)2 * pb1 + 1) * p.n1 * sizeof(C);
   size_t sm2 = ((size_t)4 * pb2 + 1) * p.n2 * sizeof(C);
@@ -418,6 +426,12 @@ int plan_fft(int64_t n, FftPlan* p) {
   for (int q = 0; q < a.nr; ++q) p->r1[q] = a.r[q];
   for (int q = 0; q < b.nr; ++q) p->r2[q] = b.r[q];
   return 0;
+}
+
+bool fft_pb_valid(const lisa_td_ctx* c, int Wpad, int pass, int pb) {
+  const size_t cs = 2 * (size_t)c->esize;
+  return pass == 1 ? pb_fits(c->plan.n1, 2, cs, Wpad / 2, pb)
+                   : pb_fits(c->plan.n2, 4, cs, Wpad / 2, pb);
 }
 
 cudaError_t launch_fft_pass1(const lisa_td_ctx* c, int Wpad, const void* r, cudaStream_t s) {

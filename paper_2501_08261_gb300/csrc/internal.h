@@ -66,6 +66,10 @@ struct lisa_td_ctx {
   int fft_col0;
   int fft_ldr;
   int64_t fft_cstride;
+  // launch shapes chosen by lisa_td_autotune (0 = built-in default): tile of
+  // the projection (samples per CTA) and its warps per CTA; columns per block
+  // of FFT pass 1 and pass 2
+  int tune_tile, tune_warps, tune_pb1, tune_pb2;
 };
 
 namespace lisa {
@@ -94,8 +98,12 @@ cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl,
 int plan_fft(int64_t n, FftPlan* p);
 // api.cu: set the thread's lisa_td_last_error() text, return `code`
 int report_error(int code, const char* fmt, ...);
-// ragged.cu: release the window views of a context
+// ragged.cu: release the window views of a context; the view of the last nv
+// samples (created on first use)
 void free_ragged(lisa_td_ctx* c);
+cudaError_t ragged_view(lisa_td_ctx* c, int64_t nv, cudaStream_t s, lisa_td_ctx** out);
+// fft.cu: whether Pb columns per block is a valid choice for pass 1 / pass 2
+bool fft_pb_valid(const lisa_td_ctx* c, int Wpad, int pass, int pb);
 // the seven stages of one likelihood evaluation on context (or view) c
 cudaError_t run_loglike_stages(const lisa_td_ctx* c, const double* params, int W, double* logl,
                                int32_t* status, cudaStream_t s, cudaEvent_t* ev);

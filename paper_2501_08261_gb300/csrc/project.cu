@@ -266,7 +266,7 @@ template <int K>
 cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* y,
                      cudaStream_t s) {
   const double dt = c->cfg.dt;
-  const int tile = 128;
+  const int tile = c->tune_tile > 0 ? c->tune_tile : 128;
   int halo = (K / 2) + 2 +
              (int)ceil((1.1 * kArmSec + kArmSec + kAUSec * kOmegaOrb * tile * dt) / dt);
   int groups = (W + 31) / 32;
@@ -274,6 +274,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
   dim3 block(32, 4);
   if (c->cfg.precision == 0) {
     size_t smem = (size_t)(tile + 2 * halo) * kPW * sizeof(double2);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(project_fp64_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     project_fp64_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
@@ -285,9 +286,10 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
     double q = kArmSec / dt;
     int nL = (int)floor(q);
     float rL = (float)(q - nL);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaFuncSetAttribute(project_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    dim3 blockm(32, 8);
+    dim3 blockm(32, c->tune_warps > 0 ? c->tune_warps : 8);
     project_mixed_kernel<K><<<grid, blockm, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                       c->orb32, (const float2*)h, (float*)y,
                                                       tile, halo, nL, rL, c->woff);

@@ -231,6 +231,13 @@ cudaError_t get_view(lisa_td_ctx* c, Ragged* r, int64_t nv, cudaStream_t s, View
 
 }  // namespace
 
+cudaError_t ragged_view(lisa_td_ctx* c, int64_t nv, cudaStream_t s, lisa_td_ctx** out) {
+  View* vw = nullptr;
+  cudaError_t e = get_view(c, state(c), nv, s, &vw);
+  if (e == cudaSuccess) *out = &vw->v;
+  return e;
+}
+
 void free_ragged(lisa_td_ctx* c) {
   Ragged* r = (Ragged*)c->ragged;
   if (!r) return;
