@@ -1,0 +1,91 @@
+"""Edge cases of the batched likelihood: a thousand walkers (ragged tail of the
+64-walker TDI groups), the smallest grids, and the mixed path at every
+Lagrange order, each against the FP64 oracle or the FP64 GPU path."""
+import numpy as np
+import pytest
+
+from oracle import pipeline
+from paper_2501_08261_gb300 import api, workloads
+
+from helpers import gpu_kwargs, oracle_setup
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    from paper_2501_08261_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def _t(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def test_thousand_walkers_mixed_vs_fp64_and_oracle():
+    cfg = workloads.config("c2_hm_1d")
+    W = 1000
+    th = workloads.prior_draws(W, cfg["n"], 5.0, 81, logm=(5.5, 7.0))
+    s = oracle_setup(cfg)
+    d = pipeline.aet(th[0], s)
+    far = th[0].copy()
+    far[8] = 1e30
+    rho = np.sqrt(-2.0 * pipeline.loglike(far, s, d))
+    d = d * (2000.0 / rho)                      # the |dlogL| <= 0.05 bar holds at SNR <= 2000
+    th[0, 8] *= rho / 2000.0
+    l64 = api.Likelihood(precision=0, max_walkers=W, **gpu_kwargs(cfg))
+    l32 = api.Likelihood(precision=1, max_walkers=W, **gpu_kwargs(cfg))
+    l64.set_data(_t(d))
+    l32.set_data(_t(d))
+    a = l64.loglike(_t(th)).cpu().numpy()
+    b = l32.loglike(_t(th)).cpu().numpy()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(b))
+    assert np.all(np.abs(a - b) <= np.maximum(0.05, 1e-4 * np.abs(a)))
+    for w in (0, 511, 999):                     # first, a middle and the last (tail) walker
+        o = pipeline.loglike(th[w], s, d)
+        assert abs(a[w] - o) <= max(1e-6, 1e-11 * abs(o)), (w, a[w], o)
+    l64.close()
+    l32.close()
+
+
+@pytest.mark.parametrize("n", [128, 640])
+def test_small_grids_match_oracle(n):
+    # grids shorter than the TDI halos and a light time: zero extension everywhere
+    cfg = workloads.config("c1_fp64_1d", n=n)
+    th = workloads.prior_draws(3, n, 5.0, 82, logm=(5.0, 5.5))
+    th[:, 14] = 0.9 * n * 5.0
+    s = oracle_setup(cfg)
+    d = pipeline.aet(th[0], s)
+    lk = api.Likelihood(precision=0, max_walkers=3, **gpu_kwargs(cfg))
+    lk.set_data(_t(d))
+    got = lk.loglike(_t(th)).cpu().numpy()
+    for w in range(3):
+        o = pipeline.loglike(th[w], s, d)
+        assert abs(got[w] - o) <= max(1e-6, 1e-11 * abs(o)), (w, got[w], o)
+    lk.close()
+
+
+@pytest.mark.parametrize("p", [1, 3, 5, 7, 15])
+def test_mixed_path_at_each_lagrange_order(p):
+    cfg = workloads.config("c2_hm_1d", n=8640, lagrange_order=p)
+    s = oracle_setup(cfg)
+    th = workloads.prior_draws(4, cfg["n"], 5.0, 83 + p, logm=(5.5, 7.0))
+    d = pipeline.aet(th[0], s)
+    # the injection at SNR 500, three walkers near it and one far away
+    far = th[0].copy()
+    far[8] = 1e30
+    rho = np.sqrt(-2.0 * pipeline.loglike(far, s, d))
+    d = d * (500.0 / rho)
+    th[0, 8] *= rho / 500.0
+    th[1:3] = th[0]
+    th[1, 14] += 2.0
+    th[2, 11] += 1e-3
+    lk = api.Likelihood(precision=1, max_walkers=4, **gpu_kwargs(cfg))
+    lk.set_data(_t(d))
+    got = lk.loglike(_t(th)).cpu().numpy()
+    for w in range(4):
+        o = pipeline.loglike(th[w], s, d)
+        assert abs(got[w] - o) <= max(0.05, 1e-4 * abs(o)), (p, w, got[w], o)
+    lk.close()
