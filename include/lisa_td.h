@@ -100,6 +100,17 @@ int lisa_td_tdi(lisa_td_ctx* ctx, const void* y_dev, int32_t W, void* aet_dev,
 int lisa_td_loglike_batch(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
                           double* logl_dev, int32_t* status_dev, void* stream);
 
+/* Coloured Gaussian noise with the likelihood's PSDs (data = signal + noise
+ * instead of the zero-noise injections of Sec. II.C; the paper's stated next
+ * step): per band bin k the noise's DFT is N_k = sqrt(n S_c(f_k) / (2 dt))
+ * (x_k + i y_k) / sqrt(2) (S_AE for A and E, S_T for T), zero outside the
+ * band, and noise_dev [3][n] (FP64) is its real inverse DFT, so that the
+ * likelihood's (n|n) equals the sum of x_k^2 + y_k^2 over the band.
+ * z_dev [3][2][n/2 + 1] FP64: the standard normals x, y of each channel and
+ * bin (the caller's random numbers; entries outside the band are unused).
+ * A set-up step (O(n x band bins) FP64 work), not part of the hot path. */
+int lisa_td_noise(lisa_td_ctx* ctx, const double* z_dev, double* noise_dev, void* stream);
+
 /* Ragged batch (walkers of uneven signal length): walker w is evaluated on
  * its own analysis window, the last n_host[w] samples of the grid (times
  * t0 + (n - n_w + j) dt, j < n_w), with the data restricted to that window

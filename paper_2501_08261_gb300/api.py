@@ -15,7 +15,7 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
-           "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune",
+           "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune", "lisa_td_noise",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
            "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept",
            "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
@@ -51,6 +51,7 @@ def load_library(path=None):
         "lisa_td_loglike_ragged": ([P, P, I32, P, P, P, P], ctypes.c_int),
         "lisa_td_ragged_graph": ([P, I32], ctypes.c_int),
         "lisa_td_autotune": ([P, P, I32, P, P, P], ctypes.c_int),
+        "lisa_td_noise": ([P, P, P, P], ctypes.c_int),
         "lisa_td_profile": ([P, I32], ctypes.c_int),
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
@@ -173,6 +174,10 @@ def lisa_td_autotune(ctx, params, W, n_per_walker=None, stream=None):
     _check(lib().lisa_td_autotune(ctx, _ptr(params), int(W), nh, ch, _stream(stream)),
            "lisa_td_autotune")
     return tuple(ch)
+
+
+def lisa_td_noise(ctx, z, noise, stream=None):
+    _check(lib().lisa_td_noise(ctx, _ptr(z), _ptr(noise), _stream(stream)), "lisa_td_noise")
 
 
 def lisa_td_ragged_graph(ctx, enable):
