@@ -74,18 +74,32 @@ int lisa_gauss_walk(const double* x_dev, const double* l_dev, const int32_t* idx
 int lisa_gauss_logq(const double* mu_dev, const double* l_dev, const int32_t* idx_host,
                     int32_t D, const double* x_dev, int32_t W, double* logq_dev, void* stream);
 
-/* One Metropolis-Hastings decision per walker for an independence proposal:
- * accept x' when log u < [logL(x') - log q(x')] - [logL(x) - log q(x)] and
+/* One Metropolis-Hastings decision per walker for an independence proposal
+ * with target pi^beta (tempered chains; beta = 1 is the posterior): accept x'
+ * when log u < [beta logL(x') - log q(x')] - [beta logL(x) - log q(x)] and
  * lo <= x' <= hi componentwise (uniform prior box; Table I's prior ranges) and
  * logL(x') > -inf.  On acceptance x, logL, log q of the walker are replaced
  * in place.  x_prop_dev [W][15], logl_prop_dev [W], logq_prop_dev [W],
- * u_dev [W] uniform in (0, 1] (the caller's random numbers), lo_host / hi_host
- * [15]; x_dev [W][15], logl_dev [W], logq_dev [W] in/out; accepted_dev [W]
- * int32 0/1 (may be NULL). */
+ * u_dev [W] uniform in (0, 1] (the caller's random numbers), beta_dev [W]
+ * inverse temperatures or NULL (all 1), lo_host / hi_host [15]; x_dev
+ * [W][15], logl_dev [W], logq_dev [W] in/out; accepted_dev [W] int32 0/1
+ * (may be NULL).  For a symmetric proposal pass log q = 0 for both. */
 int lisa_mh_accept(int32_t W, const double* x_prop_dev, const double* logl_prop_dev,
-                   const double* logq_prop_dev, const double* u_dev, const double* lo_host,
-                   const double* hi_host, double* x_dev, double* logl_dev, double* logq_dev,
-                   int32_t* accepted_dev, void* stream);
+                   const double* logq_prop_dev, const double* u_dev, const double* beta_dev,
+                   const double* lo_host, const double* hi_host, double* x_dev, double* logl_dev,
+                   double* logq_dev, int32_t* accepted_dev, void* stream);
+
+/* Parallel tempering (the sampler of Sec. II.C is ptemcee): replica exchange
+ * between adjacent temperatures for walkers stored temperature-major,
+ * x_dev [T][W][15], logl_dev / logq_dev [T][W].  betas_host [T] in (0, 1],
+ * decreasing with the index (betas[0] = 1, the posterior).  For k = T-2 down
+ * to 0 the states (x, logL, log q) of (k, w) and (k+1, w) are exchanged when
+ * log u[k][w] < (beta_k - beta_{k+1}) (logL_{k+1,w} - logL_{k,w});
+ * u_dev [T-1][W] uniform in (0, 1]; swapped_dev [T-1][W] int32 0/1 (may be
+ * NULL).  2 <= T <= 15. */
+int lisa_pt_swap(int32_t T, int32_t W, const double* betas_host, const double* u_dev,
+                 double* x_dev, double* logl_dev, double* logq_dev, int32_t* swapped_dev,
+                 void* stream);
 
 #ifdef __cplusplus
 }

@@ -99,8 +99,9 @@ def gauss_walk(x, L, idx, z, step):
     return x
 
 
-def mh_accept(x, logl, logq, xp, loglp, logqp, u, lo, hi):
-    """One independence Metropolis-Hastings decision per walker.
+def mh_accept(x, logl, logq, xp, loglp, logqp, u, lo, hi, beta=None):
+    """One independence Metropolis-Hastings decision per walker (at inverse
+    temperature beta[w], target pi^beta; beta = 1 when None).
     -> (x, logl, logq) after the step and the accepted flags (int)."""
     x = np.array(x, dtype=np.float64)
     logl = np.array(logl, dtype=np.float64)
@@ -110,9 +111,35 @@ def mh_accept(x, logl, logq, xp, loglp, logqp, u, lo, hi):
         inside = bool(np.all(xp[w] >= lo) and np.all(xp[w] <= hi))
         if not inside or not (loglp[w] > -math.inf):
             continue
-        if math.log(u[w]) < (loglp[w] - logqp[w]) - (logl[w] - logq[w]):
+        b = 1.0 if beta is None else beta[w]
+        if math.log(u[w]) < (b * loglp[w] - logqp[w]) - (b * logl[w] - logq[w]):
             x[w] = xp[w]
             logl[w] = loglp[w]
             logq[w] = logqp[w]
             acc[w] = 1
     return x, logl, logq, acc
+
+
+def pt_swap(x, logl, logq, betas, u):
+    """Replica exchange between adjacent temperatures (ptemcee-style parallel
+    tempering, the sampler of Sec. II.C): walkers are [T][W] (temperature
+    major, beta decreasing with the index, beta[0] = 1); for k = T-2 down to 0
+    the states of (k, w) and (k+1, w) are exchanged when
+    log u[k][w] < (beta_k - beta_{k+1}) (logL_{k+1,w} - logL_{k,w}).
+    x [T][W][15], logl / logq [T][W] are returned updated with the swap flags
+    [T-1][W]; log q (of the proposal at each walker's position) moves with
+    the state."""
+    x = np.array(x, dtype=np.float64)
+    logl = np.array(logl, dtype=np.float64)
+    logq = np.array(logq, dtype=np.float64)
+    T, W = logl.shape
+    sw = np.zeros((T - 1, W), dtype=np.int32)
+    for w in range(W):
+        for k in range(T - 2, -1, -1):
+            a = (betas[k] - betas[k + 1]) * (logl[k + 1, w] - logl[k, w])
+            if math.log(u[k][w]) < a:
+                x[[k, k + 1], w] = x[[k + 1, k], w]
+                logl[[k, k + 1], w] = logl[[k + 1, k], w]
+                logq[[k, k + 1], w] = logq[[k + 1, k], w]
+                sw[k, w] = 1
+    return x, logl, logq, sw

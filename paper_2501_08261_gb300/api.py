@@ -17,7 +17,7 @@ EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_pr
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
            "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune", "lisa_td_noise",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
-           "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept",
+           "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept", "lisa_pt_swap",
            "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
            "flow_logprob", "flow_propose", "flow_grad", "flow_adam", "flow_train", "flow_destroy")
 NSTAGE = 7
@@ -63,7 +63,8 @@ def load_library(path=None):
         "lisa_gauss_draw": ([P, P, P, I32, P, I32, P, P, P], ctypes.c_int),
         "lisa_gauss_logq": ([P, P, P, I32, P, I32, P, P], ctypes.c_int),
         "lisa_gauss_walk": ([P, P, P, I32, P, I32, ctypes.c_double, P, P], ctypes.c_int),
-        "lisa_mh_accept": ([I32, P, P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "lisa_mh_accept": ([I32, P, P, P, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "lisa_pt_swap": ([I32, I32, P, P, P, P, P, P, P], ctypes.c_int),
         "flow_create": ([ctypes.POINTER(P), I32, I32, I32, I32, P, P, P], ctypes.c_int),
         "flow_nparams": ([P, ctypes.POINTER(I64)], ctypes.c_int),
         "flow_set_params": ([P, P, P], ctypes.c_int),
@@ -261,11 +262,17 @@ def lisa_gauss_walk(x, l, idx, z, W, step, x_prop, stream=None):
 
 
 def lisa_mh_accept(W, x_prop, logl_prop, logq_prop, u, lo, hi, x, logl, logq, accepted=None,
-                   stream=None):
+                   stream=None, beta=None):
     (la, lp), (ha, hp) = _host_f64(lo), _host_f64(hi)
     _check(lib().lisa_mh_accept(int(W), _ptr(x_prop), _ptr(logl_prop), _ptr(logq_prop), _ptr(u),
-                                lp, hp, _ptr(x), _ptr(logl), _ptr(logq), _ptr(accepted),
-                                _stream(stream)), "lisa_mh_accept")
+                                _ptr(beta), lp, hp, _ptr(x), _ptr(logl), _ptr(logq),
+                                _ptr(accepted), _stream(stream)), "lisa_mh_accept")
+
+
+def lisa_pt_swap(T, W, betas, u, x, logl, logq, swapped=None, stream=None):
+    ba, bp = _host_f64(betas)
+    _check(lib().lisa_pt_swap(int(T), int(W), bp, _ptr(u), _ptr(x), _ptr(logl), _ptr(logq),
+                              _ptr(swapped), _stream(stream)), "lisa_pt_swap")
 
 
 def flow_create(dim, layers, hidden, max_batch, idx, perms, stream=None):

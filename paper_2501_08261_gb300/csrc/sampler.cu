@@ -153,7 +153,8 @@ __global__ void gauss_logq_kernel(const double* __restrict__ mu, const double* _
 
 __global__ void mh_accept_kernel(int W, const double* __restrict__ xp,
                                  const double* __restrict__ loglp, const double* __restrict__ logqp,
-                                 const double* __restrict__ u, SampleSpec sp, double* __restrict__ x,
+                                 const double* __restrict__ u, const double* __restrict__ beta,
+                                 SampleSpec sp, double* __restrict__ x,
                                  double* __restrict__ logl, double* __restrict__ logq,
                                  int32_t* __restrict__ accepted) {
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,13 +164,42 @@ __global__ void mh_accept_kernel(int W, const double* __restrict__ xp,
     const double v = xp[(int64_t)w * kP + k];
     ok = (v >= sp.lo[k]) && (v <= sp.hi[k]);
   }
-  if (ok) ok = log(u[w]) < (loglp[w] - logqp[w]) - (logl[w] - logq[w]);
+  const double b = beta ? beta[w] : 1.0;            // target pi^b (tempered chains)
+  if (ok) ok = log(u[w]) < (b * loglp[w] - logqp[w]) - (b * logl[w] - logq[w]);
   if (ok) {
     for (int k = 0; k < kP; ++k) x[(int64_t)w * kP + k] = xp[(int64_t)w * kP + k];
     logl[w] = loglp[w];
     logq[w] = logqp[w];
   }
   if (accepted) accepted[w] = ok ? 1 : 0;
+}
+
+// replica exchange: thread per walker column w, pairs (k, k+1) from the
+// hottest down; states [T][W] temperature-major
+__global__ void pt_swap_kernel(int T, int W, SampleSpec bt, const double* __restrict__ u,
+                               double* __restrict__ x, double* __restrict__ logl,
+                               double* __restrict__ logq, int32_t* __restrict__ swapped) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= W) return;
+  for (int k = T - 2; k >= 0; --k) {
+    const int64_t a = (int64_t)k * W + w, b = (int64_t)(k + 1) * W + w;
+    const double acc = (bt.eps[k] - bt.eps[k + 1]) * (logl[b] - logl[a]);
+    const bool s = log(u[(int64_t)k * W + w]) < acc;
+    if (s) {
+      for (int q = 0; q < kP; ++q) {
+        const double t = x[a * kP + q];
+        x[a * kP + q] = x[b * kP + q];
+        x[b * kP + q] = t;
+      }
+      double t = logl[a];
+      logl[a] = logl[b];
+      logl[b] = t;
+      t = logq[a];
+      logq[a] = logq[b];
+      logq[b] = t;
+    }
+    if (swapped) swapped[(int64_t)k * W + w] = s ? 1 : 0;
+  }
 }
 
 int spec_from(const int32_t* idx, const double* eps, int D, SampleSpec* sp) {
@@ -287,9 +317,9 @@ int lisa_gauss_logq(const double* mu_dev, const double* l_dev, const int32_t* id
 }
 
 int lisa_mh_accept(int32_t W, const double* x_prop_dev, const double* logl_prop_dev,
-                   const double* logq_prop_dev, const double* u_dev, const double* lo_host,
-                   const double* hi_host, double* x_dev, double* logl_dev, double* logq_dev,
-                   int32_t* accepted_dev, void* stream) {
+                   const double* logq_prop_dev, const double* u_dev, const double* beta_dev,
+                   const double* lo_host, const double* hi_host, double* x_dev, double* logl_dev,
+                   double* logq_dev, int32_t* accepted_dev, void* stream) {
   if (!x_prop_dev || !logl_prop_dev || !logq_prop_dev || !u_dev || !lo_host || !hi_host ||
       !x_dev || !logl_dev || !logq_dev)
     return report_error(LISA_TD_EINVAL, "NULL argument");
@@ -301,9 +331,27 @@ int lisa_mh_accept(int32_t W, const double* x_prop_dev, const double* logl_prop_
     sp.hi[k] = hi_host[k];
   }
   mh_accept_kernel<<<nb(W, 128), 128, 0, (cudaStream_t)stream>>>(
-      W, x_prop_dev, logl_prop_dev, logq_prop_dev, u_dev, sp, x_dev, logl_dev, logq_dev,
+      W, x_prop_dev, logl_prop_dev, logq_prop_dev, u_dev, beta_dev, sp, x_dev, logl_dev, logq_dev,
       accepted_dev);
   return launched("lisa_mh_accept");
+}
+
+int lisa_pt_swap(int32_t T, int32_t W, const double* betas_host, const double* u_dev,
+                 double* x_dev, double* logl_dev, double* logq_dev, int32_t* swapped_dev,
+                 void* stream) {
+  if (!betas_host || !u_dev || !x_dev || !logl_dev || !logq_dev)
+    return report_error(LISA_TD_EINVAL, "NULL argument");
+  if (T < 2 || T > kP) return report_error(LISA_TD_EINVAL, "T=%d must be in 2..15", T);
+  if (W < 1) return report_error(LISA_TD_EINVAL, "W must be >= 1");
+  SampleSpec bt;
+  memset(&bt, 0, sizeof(bt));
+  for (int k = 0; k < T; ++k) {
+    if (!(betas_host[k] > 0.0) || betas_host[k] > 1.0) return report_error(LISA_TD_EINVAL, "betas must be in (0, 1]");
+    bt.eps[k] = betas_host[k];
+  }
+  pt_swap_kernel<<<nb(W, 128), 128, 0, (cudaStream_t)stream>>>(T, W, bt, u_dev, x_dev, logl_dev,
+                                                               logq_dev, swapped_dev);
+  return launched("lisa_pt_swap");
 }
 
 }  // extern "C"

@@ -22,10 +22,13 @@ from . import api
 class MH:
     """W walkers of an MH chain on the likelihood `lik` inside the box [lo, hi]."""
 
-    def __init__(self, lik, lo, hi, W, seed=0):
+    def __init__(self, lik, lo, hi, W, seed=0, beta=None):
         import torch
         self.torch = torch
         self.lik, self.W = lik, W
+        # inverse temperature of each walker (tempered targets pi^beta), or None
+        self.beta = None if beta is None else torch.as_tensor(beta, dtype=torch.float64,
+                                                              device="cuda").contiguous()
         self.lo, self.hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
         self.gen = torch.Generator(device="cuda")
         self.gen.manual_seed(seed)
@@ -49,7 +52,7 @@ class MH:
         u = self.torch.rand(self.W, generator=self.gen, dtype=self.torch.float64, device="cuda")
         u = 1.0 - u                                        # (0, 1]
         api.lisa_mh_accept(self.W, self.xp, loglp, self.logqp, u, self.lo, self.hi, self.x,
-                           self.logl, self.logq, self.acc)
+                           self.logl, self.logq, self.acc, beta=self.beta)
         return self.acc
 
     def step_walk(self, L, idx, step):
@@ -99,6 +102,49 @@ class MH:
         if record:
             chain[:] = dev.cpu().numpy()
         return chain, float(acc.mean().item()) / steps, e0.elapsed_time(e1)
+
+
+class PT(MH):
+    """Parallel tempering (the sampler of Sec. II.C is ptemcee): T temperatures
+    x W walkers in one batch, temperature-major, betas[0] = 1; each step is an
+    MH step of every walker at its temperature followed by replica exchange
+    between adjacent temperatures (lisa_pt_swap)."""
+
+    def __init__(self, lik, lo, hi, W, betas, seed=0):
+        self.T = len(betas)
+        self.betas = np.asarray(betas, dtype=np.float64)
+        super().__init__(lik, lo, hi, self.T * W, seed, beta=np.repeat(self.betas, W))
+        self.Wt = W
+        self.swapped = self.torch.zeros(self.T * W, dtype=self.torch.int32, device="cuda")
+
+    def step_walk(self, L, idx, step):
+        """Fisher random walk at every temperature, the step widened by
+        1/sqrt(beta) (the tempered posterior's width), then replica exchange."""
+        torch = self.torch
+        z = torch.randn((self.W, len(idx)), generator=self.gen, dtype=torch.float64,
+                        device="cuda")
+        W = self.Wt
+        for k in range(self.T):
+            sl = slice(k * W, (k + 1) * W)
+            api.lisa_gauss_walk(self.x[sl], L, idx, z[sl], W, step / np.sqrt(self.betas[k]),
+                                self.xp[sl])
+        self.logqp.zero_()
+        acc = self._accept(self.lik.loglike(self.xp)).clone()
+        self.swap()
+        return acc
+
+    def swap(self):
+        torch = self.torch
+        u = 1.0 - torch.rand((self.T - 1) * self.Wt, generator=self.gen, dtype=torch.float64,
+                             device="cuda")
+        api.lisa_pt_swap(self.T, self.Wt, self.betas, u, self.x, self.logl, self.logq,
+                         self.swapped)
+        return self.swapped[:(self.T - 1) * self.Wt]
+
+
+def geometric_ladder(T, beta_min):
+    """betas[k] = beta_min^(k / (T - 1)), k = 0 .. T-1 (ptemcee's default shape)."""
+    return beta_min ** (np.arange(T) / max(T - 1, 1))
 
 
 def fisher(lik64, theta0, idx, eps):

@@ -150,3 +150,31 @@ def test_fisher_of_gpu_likelihood_matches_oracle_fisher():
     scale = np.sqrt(np.outer(np.diag(Fo), np.diag(Fo)))
     assert np.all(np.abs(F.cpu().numpy() - Fo) <= 1e-5 * scale)
     lk.close()
+
+
+def test_tempered_accept_and_swaps_match_oracle_exactly():
+    T, W = 4, 1000
+    rng = np.random.default_rng(41)
+    betas = np.array([1.0, 0.6, 0.3, 0.1])
+    beta_w = np.repeat(betas, W)
+    n = T * W
+    x, xp = rng.normal(size=(n, 15)), rng.normal(size=(n, 15))
+    logl, loglp = rng.normal(size=n) * 5 - 20, rng.normal(size=n) * 5 - 20
+    logq, logqp = rng.normal(size=n), rng.normal(size=n)
+    u = rng.uniform(1e-12, 1.0, n)
+    lo, hi = np.full(15, -9.0), np.full(15, 9.0)
+    xd, ld, qd = _t(x), _t(logl), _t(logq)
+    acc = torch.empty(n, dtype=torch.int32, device="cuda")
+    api.lisa_mh_accept(n, _t(xp), _t(loglp), _t(logqp), _t(u), lo, hi, xd, ld, qd, acc,
+                       beta=_t(beta_w))
+    xo, lo_, qo, acco = sampler.mh_accept(x, logl, logq, xp, loglp, logqp, u, lo, hi, beta_w)
+    assert np.array_equal(acc.cpu().numpy(), acco) and np.array_equal(xd.cpu().numpy(), xo)
+    us = rng.uniform(1e-12, 1.0, (T - 1) * W)
+    sw = torch.empty((T - 1) * W, dtype=torch.int32, device="cuda")
+    api.lisa_pt_swap(T, W, betas, _t(us), xd, ld, qd, sw)
+    xs, ls, qs, swo = sampler.pt_swap(xo.reshape(T, W, 15), lo_.reshape(T, W), qo.reshape(T, W),
+                                      betas, us.reshape(T - 1, W))
+    assert np.array_equal(sw.cpu().numpy().reshape(T - 1, W), swo)
+    assert np.array_equal(xd.cpu().numpy(), xs.reshape(n, 15))
+    assert np.array_equal(ld.cpu().numpy(), ls.ravel()) and np.array_equal(qd.cpu().numpy(), qs.ravel())
+    assert 0 < swo.mean() < 1

@@ -163,3 +163,39 @@ def test_random_walk_chain_targets_a_correlated_gaussian():
     s = np.concatenate(keep)
     assert np.allclose(np.cov(s.T), C, atol=0.06)
     assert np.all(np.abs(s.mean(axis=0)) < 0.05)
+
+
+def test_tempered_chains_and_swaps_target_the_tempered_posteriors():
+    # target N(0, 1) on parameter 0; at inverse temperature b the chain samples
+    # N(0, 1/b), whatever the swaps between temperatures do
+    betas = np.array([1.0, 0.5, 0.25])
+    T, W = 3, 128
+    rng = np.random.default_rng(9)
+    mu = np.zeros(15)
+    L = np.array([[1.0 / 2.5]])                       # proposal N(0, 2.5^2)
+    lo, hi = np.full(15, -40.0), np.full(15, 40.0)
+    beta_w = np.repeat(betas, W)
+
+    def logl_of(x):
+        return -0.5 * x[:, 0] ** 2
+
+    x, logq = sampler.gauss_draw(mu, L, [0], rng.normal(size=(T * W, 1)))
+    logl = logl_of(x)
+    keep = [[] for _ in range(T)]
+    nsw = 0
+    for it in range(700):
+        xp, logqp = sampler.gauss_draw(mu, L, [0], rng.normal(size=(T * W, 1)))
+        x, logl, logq, _ = sampler.mh_accept(x, logl, logq, xp, logl_of(xp), logqp,
+                                             rng.uniform(1e-300, 1.0, T * W), lo, hi, beta_w)
+        xs, ls, qs, sw = sampler.pt_swap(x.reshape(T, W, 15), logl.reshape(T, W),
+                                         logq.reshape(T, W), betas,
+                                         rng.uniform(1e-300, 1.0, (T - 1, W)))
+        x, logl, logq = xs.reshape(T * W, 15), ls.ravel(), qs.ravel()
+        nsw += sw.sum()
+        if it >= 100:
+            for k in range(T):
+                keep[k].append(xs[k, :, 0].copy())
+    for k in range(T):
+        v = np.concatenate(keep[k]).var()
+        assert abs(v * betas[k] - 1.0) < 0.06, (k, v)
+    assert nsw > 0
