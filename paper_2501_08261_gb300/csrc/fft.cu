@@ -287,8 +287,13 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   const C* X = transform(u0, u1, n2, P2, rd, (const C*)tws);
   const int64_t nb = n / 2 + 1;
   const double* wv = psdw + (c == 2 ? nb : 0);
-  double accx = 0.0, accy = 0.0;     // walker 2p, 2p+1 (p fixed per thread); FP64: the
-                                     // weights 4 df dt^2 / S reach ~1e47, beyond FP32
+  // walker 2p, 2p+1 (p fixed per thread).  FP64 transforms accumulate in FP64.
+  // FP32 transforms accumulate in FP32 with exact power-of-two scalings: the
+  // weights 4 df dt^2 / S reach 1e47 (x 2^-160: <= 1) and the spectra of
+  // small residuals 1e-20 (x 2^64), so every product stays in FP32's normal
+  // range; the per-thread sums are undone by 2^(160 - 128) in FP64 below
+  double accx = 0.0, accy = 0.0;
+  float faccx = 0.0f, faccy = 0.0f;
   const int nrow = single ? 1 : 2;
   for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
     const int k2 = item / Pb, p = item % Pb;
@@ -303,11 +308,25 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
       const int km = (single && row == 0) ? (n2 - k2) % n2 : n2 - 1 - k2;
       C z = X[k2 * P2 + co + p];
       C zm = X[km * P2 + cm + p];
-      const double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
-      const double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
-      accx += wk * (xr * xr + xi * xi);
-      accy += wk * (yr * yr + yi * yi);
+      if constexpr (sizeof(R) == 4) {
+        const float ws = (float)(wk * 0x1p-160);
+        const float zx = z.x * 0x1p64f, zy = z.y * 0x1p64f;
+        const float mx = zm.x * 0x1p64f, my = zm.y * 0x1p64f;
+        const float xr = 0.5f * (zx + mx), xi = 0.5f * (zy - my);
+        const float yr = 0.5f * (zy + my), yi = -0.5f * (zx - mx);
+        faccx = fmaf(ws, fmaf(xr, xr, xi * xi), faccx);
+        faccy = fmaf(ws, fmaf(yr, yr, yi * yi), faccy);
+      } else {
+        const double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
+        const double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
+        accx += wk * (xr * xr + xi * xi);
+        accy += wk * (yr * yr + yi * yi);
+      }
     }
+  }
+  if constexpr (sizeof(R) == 4) {
+    accx = (double)faccx * 0x1p32;
+    accy = (double)faccy * 0x1p32;
   }
   // per-column reduction: thread t always served column t % Pb (blockDim % Pb == 0)
   const int p = threadIdx.x % Pb;
