@@ -1,8 +1,9 @@
 """One walker end to end: parameters -> h+, hx -> y_slr -> X,Y,Z -> A,E,T
 -> logL (Sec. II.A - II.B), FP64.
 
-``Setup`` mirrors the per-run configuration (grid, band, TDI generation,
-channel mask, Lagrange order, orbit model, mode mask, precessing flag).
+``Setup`` mirrors the per-run configuration (grid, band, TDI generation and
+delay form, channel mask, Lagrange order, orbit model, mode mask, precessing
+flag).
 """
 from dataclasses import dataclass
 
@@ -24,6 +25,7 @@ class Setup:
     orbit: str = "rigid"          # "rigid" | "kepler"
     mode_mask: int = 1            # bit0 (2,2) .. bit4 (4,4)
     precessing: bool = False
+    tdi_nested: bool = False      # TDI delays as nested operator products
 
 
 def grid(s: Setup, n=None):
@@ -51,7 +53,7 @@ def aet(theta, s: Setup, n=None, idx=None):
                                s.lagrange_order)
     else:
         need = response.tdi_support(idx, n, s.dt, s.orbit, s.tdi_gen,
-                                    s.lagrange_order, s.t0)
+                                    s.lagrange_order, s.t0, s.tdi_nested)
         part = response.all_links(hp, hc, s.t0, s.dt, s.orbit, theta[11], theta[12],
                                   s.lagrange_order, need)
         y = {}
@@ -60,7 +62,7 @@ def aet(theta, s: Setup, n=None, idx=None):
             full[need] = vals
             y[l] = full
     X, Y, Z = response.tdi_xyz(y, n, s.t0, s.dt, s.orbit, s.tdi_gen,
-                               s.lagrange_order, idx)
+                               s.lagrange_order, idx, s.tdi_nested)
     return np.stack(response.aet_from_xyz(X, Y, Z))
 
 

@@ -8,7 +8,9 @@ Readings of the paper taken here (each listed in the design doc):
 * y_slr = [x+ dh+ + 2 x_x dh_x] / (2 (1 - k.n)), i.e. n_i n_j h_ij / 2 with
   e_x = u(x)v + v(x)u; positions in light-seconds; sender at t - L_l(t).
 * every TDI delay is the plain sum of the light times evaluated at the
-  output time t.
+  output time t (the printed form); with ``nested=True`` each term's delay is
+  instead the product of one-link delay operators, applied from the output
+  time backwards (the chains below).
 * the third y_123 term of X_2 carries the delay 2L_-2 + L_2 + 2L_3 + 2L_-3.
 """
 import math
@@ -38,6 +40,34 @@ X20_TERMS = (
 )
 
 
+# The same terms with each delay as a product of one-link operators,
+# D_a f(t) = f(t - L_a(t)), the first link of a chain applied at the output
+# time and each next one at the output time minus the delay so far.  Writing
+# D_ijk.. for the path received at i from j, at j from k, ..., X factors as
+#   X_1.5 = (1 - D_121)(y_{3-21} + D_13 y_123) - (1 - D_131)(y_231 + D_12 y_{1-32})
+#   X_2   = (1 - D_121 - D_12131 + D_1312121)(y_{3-21} + D_13 y_123)
+#         - (1 - D_131 - D_13121 + D_1213131)(y_231 + D_12 y_{1-32}),
+# and every printed term is exactly one product of that expansion (same link,
+# sign and multiset of light times).  D_12 is link 3, D_21 link -3, D_13
+# link -2, D_31 link 2.  Order and entries follow X15_TERMS / X20_TERMS.
+X15_CHAINS = (
+    (-3, +1, (-2, 2, 3)), (-3, -1, (3,)),
+    (3, +1, (-2, 2)), (3, -1, ()),
+    (2, +1, (-2,)), (2, -1, (3, -3, -2)),
+    (-2, +1, ()), (-2, -1, (3, -3)),
+)
+X20_CHAINS = (
+    (-3, +1, (-2, 2, 3)), (-3, -1, (3,)),
+    (-3, +1, (-2, 2, 3, -3, 3)), (-3, -1, (3, -3, -2, 2, -2, 2, 3)),
+    (3, +1, (-2, 2)), (3, -1, ()),
+    (3, +1, (-2, 2, 3, -3)), (3, -1, (3, -3, -2, 2, -2, 2)),
+    (2, +1, (-2,)), (2, -1, (3, -3, -2)),
+    (2, +1, (-2, 2, 3, -3, 3, -3, -2)), (2, -1, (3, -3, -2, 2, -2)),
+    (-2, +1, ()), (-2, -1, (3, -3)),
+    (-2, +1, (-2, 2, 3, -3, 3, -3)), (-2, -1, (3, -3, -2, 2)),
+)
+
+
 def cyclic(link, times=1):
     """Index permutation 1 -> 2 -> 3 -> 1 on |l|, sign kept (Y: once, Z: twice)."""
     a = abs(link)
@@ -46,9 +76,13 @@ def cyclic(link, times=1):
     return a if link > 0 else -a
 
 
-def channel_terms(gen, channel):
-    """Terms of X (channel 0), Y (1) or Z (2) for TDI generation 15 or 20."""
-    base = X15_TERMS if gen == 15 else X20_TERMS
+def channel_terms(gen, channel, nested=False):
+    """Terms of X (channel 0), Y (1) or Z (2) for TDI generation 15 or 20
+    (delay links in operator order when ``nested``)."""
+    if nested:
+        base = X15_CHAINS if gen == 15 else X20_CHAINS
+    else:
+        base = X15_TERMS if gen == 15 else X20_TERMS
     return [(cyclic(l, channel), sg, tuple(cyclic(d, channel) for d in dl))
             for (l, sg, dl) in base]
 
@@ -138,20 +172,42 @@ def all_links(hp, hc, t0, dt, orbit, beta, lam, p, idx=None):
 # TDI and A, E, T
 # ---------------------------------------------------------------------------
 
-def tdi_xyz(y, n, t0, dt, orbit, gen, p, idx=None):
+def nested_delay(orbit, chain, t):
+    """Delay of the operator product D_{c1} D_{c2} ... at output times t:
+    tau = 0, then tau += L_c(t - tau) for each link c in operator order."""
+    t = np.asarray(t, dtype=np.float64)
+    tau = np.zeros(t.shape)
+    for c in chain:
+        tau = tau + orbits.light_time(orbit, c, t - tau)
+    return tau
+
+
+def term_delays(orbit, gen, channel, t, nested=False):
+    """(link, sign, delay at t) of every term of one channel."""
+    out = []
+    if nested:
+        for (link, sign, chain) in channel_terms(gen, channel, True):
+            out.append((link, sign, nested_delay(orbit, chain, t)))
+        return out
+    L = {l: orbits.light_time(orbit, l, t) for l in orbits.LINKS}
+    for (link, sign, delays) in channel_terms(gen, channel):
+        D = np.zeros(np.shape(t))
+        for d in delays:
+            D = D + L[d]
+        out.append((link, sign, D))
+    return out
+
+
+def tdi_xyz(y, n, t0, dt, orbit, gen, p, idx=None, nested=False):
     """X, Y, Z at grid indices idx (default all) from y[link] on the full grid."""
     if idx is None:
         idx = np.arange(n)
     idx = np.asarray(idx)
     t = t0 + idx.astype(np.float64) * dt
-    L = {l: orbits.light_time(orbit, l, t) for l in orbits.LINKS}
     out = []
     for ch in range(3):
         acc = np.zeros(idx.shape)
-        for (link, sign, delays) in channel_terms(gen, ch):
-            D = np.zeros(idx.shape)
-            for d in delays:
-                D = D + L[d]
+        for (link, sign, D) in term_delays(orbit, gen, ch, t, nested):
             acc = acc + sign * interp(y[link], idx - D / dt, p)
         out.append(acc)
     return out
@@ -163,18 +219,14 @@ def aet_from_xyz(X, Y, Z):
             (X + Y + Z) / math.sqrt(3.0))
 
 
-def tdi_support(idx, n, dt, orbit, gen, p, t0=0.0):
+def tdi_support(idx, n, dt, orbit, gen, p, t0=0.0, nested=False):
     """Grid indices of y that the TDI outputs at idx read (for sparse runs)."""
     idx = np.asarray(idx)
     t = t0 + idx * dt
-    L = {l: orbits.light_time(orbit, l, t) for l in orbits.LINKS}
     o = lagrange_offsets(p)
     need = set()
     for ch in range(3):
-        for (link, sign, delays) in channel_terms(gen, ch):
-            D = np.zeros(idx.shape)
-            for d in delays:
-                D = D + L[d]
+        for (link, sign, D) in term_delays(orbit, gen, ch, t, nested):
             base = np.floor(idx - D / dt).astype(np.int64)
             for b in base:
                 need.update((b + o).tolist())

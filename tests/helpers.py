@@ -13,14 +13,16 @@ def oracle_setup(cfg):
                           channel_mask=cfg["channel_mask"],
                           lagrange_order=cfg["lagrange_order"],
                           orbit=ORBIT_NAMES[cfg["orbit"]], mode_mask=cfg["mode_mask"],
-                          precessing=bool(cfg["precessing"]))
+                          precessing=bool(cfg["precessing"]),
+                          tdi_nested=bool(cfg.get("tdi_nested", 0)))
 
 
 def gpu_kwargs(cfg):
     return dict(dt=cfg["dt"], n=cfg["n"], t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
                 tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
                 lagrange_order=cfg["lagrange_order"], orbit=cfg["orbit"],
-                mode_mask=cfg["mode_mask"], precessing=cfg["precessing"])
+                mode_mask=cfg["mode_mask"], precessing=cfg["precessing"],
+                tdi_nested=cfg.get("tdi_nested", 0))
 
 
 def norm_rel(got, want):

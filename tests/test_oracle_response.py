@@ -245,3 +245,77 @@ def test_aet_special_combinations():
     assert np.allclose(A, 0) and np.allclose(E, 0) and np.allclose(T, math.sqrt(3) * X)
     A, E, T = response.aet_from_xyz(X, 0 * X, -X)       # X = -Z, Y = 0
     assert np.allclose(A, -math.sqrt(2) * X) and np.allclose(E, 0) and np.allclose(T, 0)
+
+
+# ------------------------------------------------ nested delay operators ---
+@pytest.mark.parametrize("gen", [15, 20])
+def test_nested_chains_are_the_printed_terms(gen):
+    """Each operator chain carries the link, sign and multiset of light times
+    of the printed term it stands for (Sec. II.B, X_1.5 and X_2)."""
+    printed = response.X15_TERMS if gen == 15 else response.X20_TERMS
+    chains = response.X15_CHAINS if gen == 15 else response.X20_CHAINS
+    assert len(chains) == len(printed)
+    for (l, s, d), (lc, sc, c) in zip(printed, chains):
+        assert (l, s, sorted(d)) == (lc, sc, sorted(c))
+    for ch in range(3):
+        for (l, s, d), (lc, sc, c) in zip(response.channel_terms(gen, ch),
+                                          response.channel_terms(gen, ch, nested=True)):
+            assert (l, s, sorted(d)) == (lc, sc, sorted(c))
+
+
+@pytest.mark.parametrize("orbit", ["rigid", "static_kepler"])
+def test_nested_delays_equal_sums_for_constant_arms(orbit):
+    t = np.linspace(0.0, 5e6, 50)
+    for gen in (15, 20):
+        for ch in range(3):
+            a = response.term_delays(orbit, gen, ch, t)
+            b = response.term_delays(orbit, gen, ch, t, nested=True)
+            for (l, s, D), (lb, sb, Db) in zip(a, b):
+                assert (l, s) == (lb, sb)
+                assert np.max(np.abs(D - Db)) <= 1e-13
+
+
+def _laser_xyz(gen, nested, t, lasers):
+    """X, Y, Z of pure laser noise, one laser p_k per craft, evaluated exactly:
+    y_l(t) = p_s(t - L_l(t)) - p_r(t) for link l from s to r.  Each laser phase
+    is taken as its phase at the output time t plus 2 pi f u for the (small)
+    offset u (angle-addition formula), so that FP64 rounding of the large
+    phase at t (~1e-10 rad at 5e6 s) is common to all terms and cancels."""
+    def p(k, u):
+        out = 0.0
+        for (a, f, ph) in lasers[k]:
+            base = 2 * math.pi * f * t + ph
+            out = out + a * (np.sin(base) * np.cos(2 * math.pi * f * u)
+                             + np.cos(base) * np.sin(2 * math.pi * f * u))
+        return out
+
+    def y(link, u):
+        s, r = orbits.LINK_ENDS[link]
+        return p(s, u - orbits.light_time("kepler", link, t + u)) - p(r, u)
+
+    out = []
+    for ch in range(3):
+        acc = np.zeros(t.shape)
+        for (link, sign, D) in response.term_delays("kepler", gen, ch, t, nested):
+            acc = acc + sign * y(link, -D)
+        out.append(acc)
+    return out
+
+
+def test_tdi2_nested_operators_cancel_laser_noise():
+    """The defining property of second-generation TDI: with the delays applied
+    as nested operators on flexing (Keplerian) arms, laser noise cancels to
+    first order in the arm rates, so the residual is FP64 rounding of O(1)
+    samples.  The printed commuting sums, and X_1.5 even with nested delays,
+    leave a residual ~ p' L dL/dt ~ 1e-7 for dL/dt ~ 3e-9 (a wrong chain
+    order, sign or evaluation time fails the first bound)."""
+    rng = np.random.default_rng(11)
+    lasers = {k: [(rng.uniform(0.5, 1.0), rng.uniform(1e-3, 2e-2), rng.uniform(0, 2 * math.pi))
+                  for _ in range(4)] for k in (1, 2, 3)}
+    t = np.linspace(200.0, 60 * 86400.0, 120)
+    r2n = max(np.max(np.abs(v)) for v in _laser_xyz(20, True, t, lasers))
+    r2c = max(np.max(np.abs(v)) for v in _laser_xyz(20, False, t, lasers))
+    r15n = max(np.max(np.abs(v)) for v in _laser_xyz(15, True, t, lasers))
+    assert r2n < 2e-12
+    assert r2c > 1e-9 and r15n > 1e-9
+    assert r2n < 1e-4 * min(r2c, r15n)
