@@ -244,6 +244,34 @@ def ragged_measure(torch, api, workloads, dev, steps, W=256):
             "max_abs_dlogL_bulk": float(d[:8].max()), "graph": True}
 
 
+def nested_measure(torch, api, kw, params, aet, l_summed, steps):
+    """The headline workload with TDI delays as nested one-link operators
+    (tdi_nested = 1): the step is unchanged apart from the per-tile weights,
+    so this reports its throughput and how far logL moves from the summed
+    delays on the walkers near the injection."""
+    W = params.shape[0]
+    lk = api.Likelihood(precision=1, max_walkers=W, tdi_nested=1, **kw)
+    lk.set_data(aet)
+    logl = torch.empty(W, dtype=torch.float64, device=params.device)
+    stream = torch.cuda.current_stream()
+    api.lisa_td_autotune(lk.ctx, params, W)
+    for _ in range(3):
+        api.lisa_td_loglike_batch(lk.ctx, params, W, logl, None, stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        api.lisa_td_loglike_batch(lk.ctx, params, W, logl, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    d = (logl[:8] - l_summed[:8]).abs().max().item()
+    lk.close()
+    return {"value": round(W * steps / (ms * 1e-3), 2), "unit": "logL evals/s",
+            "ms_per_step": round(ms / steps, 3), "steps": steps,
+            "max_abs_dlogL_nested_vs_summed_bulk": d}
+
+
 def run_ours(args):
     ws, rank, lrank = _dist()
     torch, api, workloads = _setup_gpu(lrank)
@@ -370,6 +398,8 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, theta[0], aet.cpu().numpy())
+    if not args.no_nested:
+        out["nested"] = nested_measure(torch, api, kw, params, aet, l32, max(2, args.steps // 2))
     if not args.no_ragged:
         out["ragged"] = ragged_measure(torch, api, workloads, dev, max(2, args.steps // 2))
     if not args.no_proposals:
@@ -436,6 +466,8 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-proposals", action="store_true",
                     help="skip the flow vs Fisher-Gaussian proposal measurement")
+    ap.add_argument("--no-nested", action="store_true",
+                    help="skip the nested-delay TDI measurement")
     ap.add_argument("--no-ragged", action="store_true",
                     help="skip the uneven-duration (ragged) batch measurement")
     args = ap.parse_args()

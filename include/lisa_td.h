@@ -62,6 +62,12 @@ typedef struct {
   int32_t precessing;      /* 0 aligned spins, 1 precessing twist-up             */
   int32_t precision;       /* 0 FP64, 1 mixed                                    */
   int32_t max_walkers;     /* workspace is sized for this many walkers (>= 1)    */
+  int32_t tdi_nested;      /* 0: every TDI delay is the printed sum of light times
+                            * at the output time (Sec. II.B); 1: each delay is the
+                            * product of one-link operators D_l f(t) = f(t - L_l(t)),
+                            * applied from the output time backwards (the ordering
+                            * of the standard factorised X_1.5 / X_2).  Equal for
+                            * rigid orbits.                                        */
 } lisa_td_config;
 
 /* Create a context: validates cfg, builds the orbit tables (one kernel, FP64),

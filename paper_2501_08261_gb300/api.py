@@ -31,7 +31,8 @@ class Config(ctypes.Structure):
                 ("tdi_gen", ctypes.c_int32), ("channel_mask", ctypes.c_int32),
                 ("lagrange_order", ctypes.c_int32), ("orbit_kind", ctypes.c_int32),
                 ("mode_mask", ctypes.c_int32), ("precessing", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("max_walkers", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("max_walkers", ctypes.c_int32),
+                ("tdi_nested", ctypes.c_int32)]
 
 
 def load_library(path=None):
@@ -119,10 +120,10 @@ def _stream(stream):
 
 def make_config(dt, n, t0=0.0, f_lo=1e-4, f_hi=0.02, tdi_gen=15, channel_mask=7,
                 lagrange_order=31, orbit=0, mode_mask=1, precessing=0, precision=0,
-                max_walkers=32):
+                max_walkers=32, tdi_nested=0):
     return Config(float(dt), int(n), float(t0), float(f_lo), float(f_hi), int(tdi_gen),
                   int(channel_mask), int(lagrange_order), int(orbit), int(mode_mask),
-                  int(precessing), int(precision), int(max_walkers))
+                  int(precessing), int(precision), int(max_walkers), int(tdi_nested))
 
 
 def lisa_td_create(cfg, stream=None):

@@ -64,6 +64,7 @@ int check_cfg(const lisa_td_config* g) {
   if (g->precessing != 0 && g->precessing != 1) return fail(LISA_TD_EINVAL, "precessing must be 0 or 1");
   if (g->precision != 0 && g->precision != 1) return fail(LISA_TD_EINVAL, "precision must be 0 or 1");
   if (g->max_walkers < 1 || g->max_walkers > 65536) return fail(LISA_TD_ERANGE, "max_walkers out of [1, 65536]");
+  if (g->tdi_nested != 0 && g->tdi_nested != 1) return fail(LISA_TD_EINVAL, "tdi_nested must be 0 or 1");
   return LISA_TD_OK;
 }
 

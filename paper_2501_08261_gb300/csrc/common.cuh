@@ -124,6 +124,7 @@ struct TdiTable {
   int nterm[kNLink];              // terms that read link l (4 for TDI 1.5, 8 for TDI 2)
   TdiTerm term[kNLink][8];
   int8_t dterm[kNLink][8];        // index among the delayed terms, -1 if undelayed
+  int8_t chain[kNLink][8][8];     // term's delay links in operator order (first: at t)
   int n_dterms;
   int max_links_in_delay;
 };

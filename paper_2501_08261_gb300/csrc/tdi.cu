@@ -1,7 +1,9 @@
 // TDI Michelson X (generation 1.5 or 2.0), Y and Z by cyclic permutation, and
 // A, E, T (Sec. II.B).  Every delayed term y_l(t - D(t)) takes D(t) as the plain
-// sum of the link light times at the output time t and interpolates y with the
-// centred Lagrange stencil; undelayed terms read y_l(t) directly.
+// sum of the link light times at the output time t (the printed form) or, with
+// tdi_nested, as the product of one-link delay operators applied from t
+// backwards, and interpolates y with the centred Lagrange stencil; undelayed
+// terms read y_l(t) directly.
 //
 // Layout: one CTA = 32 walkers (lanes) x a tile of output samples.  The kernel
 // stages one link's y window at a time in shared memory and adds that link's
@@ -18,20 +20,28 @@ namespace {
 
 // X as printed (Sec. II.B): (link l, sign, links of the delay), y_{1-32} = link
 // -3, y_{231} = 3, y_{123} = 2, y_{3-21} = -2.  TDI 2: the third y_123 term is
-// read with delay 2L-2 + L2 + 2L3 + 2L-3.
+// read with delay 2L-2 + L2 + 2L3 + 2L-3.  The printed sums fix only how often
+// each light time enters a delay; the links are listed here in the operator
+// order of the factorised combinations (D_12 = link 3, D_21 = -3, D_13 = -2,
+// D_31 = 2; D_121 = D_12 D_21, ...)
+//   X_1.5 = (1 - D_121)(y_{3-21} + D_13 y_123) - (1 - D_131)(y_231 + D_12 y_{1-32}),
+//   X_2   = (1 - D_121 - D_12131 + D_1312121)(y_{3-21} + D_13 y_123)
+//         - (1 - D_131 - D_13121 + D_1213131)(y_231 + D_12 y_{1-32}),
+// of which every printed term is exactly one product; the nested form uses
+// that order, the summed form only the counts.
 struct HostTerm { int l, sign, nd, d[8]; };
 const HostTerm kX15[8] = {
-    {-3, +1, 3, {3, 2, -2}}, {-3, -1, 1, {3}}, {3, +1, 2, {2, -2}}, {3, -1, 0, {}},
-    {2, +1, 1, {-2}}, {2, -1, 3, {-2, -3, 3}}, {-2, +1, 0, {}}, {-2, -1, 2, {-3, 3}}};
+    {-3, +1, 3, {-2, 2, 3}}, {-3, -1, 1, {3}}, {3, +1, 2, {-2, 2}}, {3, -1, 0, {}},
+    {2, +1, 1, {-2}}, {2, -1, 3, {3, -3, -2}}, {-2, +1, 0, {}}, {-2, -1, 2, {3, -3}}};
 const HostTerm kX20[16] = {
-    {-3, +1, 3, {3, 2, -2}}, {-3, -1, 1, {3}},
-    {-3, +1, 5, {-2, 2, 3, 3, -3}}, {-3, -1, 7, {3, 3, -3, -2, -2, 2, 2}},
-    {3, +1, 2, {2, -2}}, {3, -1, 0, {}},
-    {3, +1, 4, {-2, 2, 3, -3}}, {3, -1, 6, {3, -3, -2, -2, 2, 2}},
-    {2, +1, 1, {-2}}, {2, -1, 3, {-2, -3, 3}},
-    {2, +1, 7, {-2, -2, 2, 3, 3, -3, -3}}, {2, -1, 5, {3, -3, -2, -2, 2}},
-    {-2, +1, 0, {}}, {-2, -1, 2, {-3, 3}},
-    {-2, +1, 6, {-2, 2, 3, 3, -3, -3}}, {-2, -1, 4, {3, -3, -2, 2}}};
+    {-3, +1, 3, {-2, 2, 3}}, {-3, -1, 1, {3}},
+    {-3, +1, 5, {-2, 2, 3, -3, 3}}, {-3, -1, 7, {3, -3, -2, 2, -2, 2, 3}},
+    {3, +1, 2, {-2, 2}}, {3, -1, 0, {}},
+    {3, +1, 4, {-2, 2, 3, -3}}, {3, -1, 6, {3, -3, -2, 2, -2, 2}},
+    {2, +1, 1, {-2}}, {2, -1, 3, {3, -3, -2}},
+    {2, +1, 7, {-2, 2, 3, -3, 3, -3, -2}}, {2, -1, 5, {3, -3, -2, 2, -2}},
+    {-2, +1, 0, {}}, {-2, -1, 2, {3, -3}},
+    {-2, +1, 6, {-2, 2, 3, -3, 3, -3}}, {-2, -1, 4, {3, -3, -2, 2}}};
 
 inline int link_index(int l) { return l > 0 ? l - 1 : 2 - l; }
 inline int cyc(int l, int times) {
@@ -55,7 +65,11 @@ TdiTable build_tdi_table(int gen) {
       t.chan = (int8_t)ch;
       t.sign = (int8_t)X[q].sign;
       t.ndelay = (int8_t)X[q].nd;
-      for (int d = 0; d < X[q].nd; ++d) t.cnt[link_index(cyc(X[q].d[d], ch))]++;
+      for (int d = 0; d < X[q].nd; ++d) {
+        const int li = link_index(cyc(X[q].d[d], ch));
+        t.cnt[li]++;
+        T.chain[j][T.nterm[j] - 1][d] = (int8_t)li;
+      }
       if (X[q].nd > T.max_links_in_delay) T.max_links_in_delay = X[q].nd;
     }
   }
@@ -77,12 +91,44 @@ __device__ inline bool group_inactive(const int64_t* __restrict__ wo, int cnt, i
   return m >= end;
 }
 
+// light time of link li at fractional grid position x: cubic Lagrange through
+// four rows of the FP64 orbit table (stencil clamped inside the table, so the
+// first and last rows extrapolate; L varies on the orbital time scale, so the
+// interpolation error is far below the table's own rounding)
+__device__ inline double light_time_at(const OrbitRec64* __restrict__ orb, int64_t n, int li,
+                                       double x) {
+  int64_t b = (int64_t)floor(x) - 1;
+  b = b < 0 ? 0 : (b > n - 4 ? n - 4 : b);
+  const double u = x - (double)b;
+  const double w0 = -(u - 1.0) * (u - 2.0) * (u - 3.0) * (1.0 / 6.0);
+  const double w1 = u * (u - 2.0) * (u - 3.0) * 0.5;
+  const double w2 = -u * (u - 1.0) * (u - 3.0) * 0.5;
+  const double w3 = u * (u - 1.0) * (u - 2.0) * (1.0 / 6.0);
+  return w0 * orb[b].L[li] + w1 * orb[b + 1].L[li] + w2 * orb[b + 2].L[li] +
+         w3 * orb[b + 3].L[li];
+}
+
+// delay D(t_i) [s] of a term: the sum of its light times at t_i, or (nested)
+// tau = 0, tau += L_c(t_i - tau) over its links c in operator order
+__device__ inline double term_delay_at(const TdiTerm& T, const int8_t* __restrict__ chain,
+                                       const OrbitRec64* __restrict__ orb, int64_t n, int64_t i,
+                                       double dt, int nested) {
+  double D = 0.0;
+  if (!nested) {
+#pragma unroll
+    for (int l = 0; l < kNLink; ++l) D += (double)T.cnt[l] * orb[i].L[l];
+    return D;
+  }
+  for (int k = 0; k < T.ndelay; ++k) D += light_time_at(orb, n, chain[k], (double)i - D / dt);
+  return D;
+}
+
 template <int K, int SPT>
 __global__ void __launch_bounds__(128) tdi_fp64_kernel(
     const TdiTable* __restrict__ tab, int W, int ldw_in, int ldw_out, int64_t n, double dt,
     const OrbitRec64* __restrict__ orb,
     const double* __restrict__ y, double* __restrict__ out, const double* __restrict__ data,
-    int resid, int hl, int hr, const int64_t* __restrict__ woff) {
+    int resid, int hl, int hr, const int64_t* __restrict__ woff, int nested) {
   constexpr int NW = 4;
   constexpr int TILE = NW * SPT;
   extern __shared__ double ywin[];              // [(TILE + hl + hr)][kPW]
@@ -123,10 +169,7 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
         if (T.ndelay == 0) {
           v = ywin[(ls + hl) * kPW + lane];
         } else {
-          const double* L = orb[i].L;
-          double D = 0.0;
-#pragma unroll
-          for (int l = 0; l < kNLink; ++l) D += (double)T.cnt[l] * L[l];
+          const double D = term_delay_at(T, tab->chain[j][q], orb, n, i, dt, nested);
           double tau = (double)(i - lo) - D / dt;    // relative to the window start
           double fl = floor(tau);
           double wts[K];
@@ -201,15 +244,9 @@ __device__ void lagrange_weights_f64(double eps, int K, double* w) {
   }
 }
 
-__device__ inline double term_delay(const TdiTerm& T, const OrbitRec64& O) {
-  double D = 0.0;
-  for (int l = 0; l < kNLink; ++l) D += (double)T.cnt[l] * O.L[l];
-  return D;
-}
-
 __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
                                  const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
-                                 int ntiles, TdiTileTerm* __restrict__ out) {
+                                 int ntiles, int nested, TdiTileTerm* __restrict__ out) {
   const int nd = tab->n_dterms;
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= (int64_t)ntiles * nd) return;
@@ -222,7 +259,7 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
   const int64_t ia = (int64_t)tile * kTdiTile;
   auto tau_rel = [&](int j) -> double {          // tau(i) - i at i = ia + j
     int64_t i = ia + j < n ? ia + j : n - 1;
-    return -term_delay(T, orb[i]) / dt;
+    return -term_delay_at(T, tab->chain[jl][q], orb, n, i, dt, nested) / dt;
   };
   const double ta = tau_rel(0);
   const double fl = floor(ta);
@@ -550,7 +587,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
                          (int)smem);
     tdi_fp64_kernel<K, SPT><<<grid, block, smem, s>>>(
         c->tdi_tab, W, ldw, ldw, c->n, dt, c->orb64, (const double*)y, (double*)out, c->data64,
-        resid, hl, hr, c->woff);
+        resid, hl, hr, c->woff, c->cfg.tdi_nested);
   } else {
     int hlm = (int)ceil(nd * 1.1 * kArmSec / dt) + K / 2 + 3;
     int hrm = K / 2 + 2;
@@ -572,7 +609,8 @@ cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s) {
   const int ntiles = (int)((c->n + kTdiTile - 1) / kTdiTile);
   const int64_t m = (int64_t)ntiles * c->n_dterms;
   tdi_tiles_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
-      c->tdi_tab, c->orb64, c->n, c->cfg.dt, c->cfg.lagrange_order + 1, ntiles, c->tdi_tiles);
+      c->tdi_tab, c->orb64, c->n, c->cfg.dt, c->cfg.lagrange_order + 1, ntiles,
+      c->cfg.tdi_nested, c->tdi_tiles);
   return cudaGetLastError();
 }
 

@@ -41,9 +41,10 @@ def test_binding_covers_the_header():
 
 
 def test_config_struct_layout_matches_header():
-    # 5 doubles / int64 then 8 int32 fields, no padding
-    assert ctypes.sizeof(api.Config) == 5 * 8 + 8 * 4
+    # 5 doubles / int64 then 9 int32 fields, padded to the 8-byte alignment
+    assert ctypes.sizeof(api.Config) == 5 * 8 + 9 * 4 + 4
     assert api.Config.tdi_gen.offset == 40 and api.Config.max_walkers.offset == 68
+    assert api.Config.tdi_nested.offset == 72
 
 
 def test_argument_errors_need_no_gpu(libpath):
@@ -55,6 +56,9 @@ def test_argument_errors_need_no_gpu(libpath):
     bad = api.make_config(dt=5.0, n=17281)
     rc = lib.lisa_td_create(ctypes.byref(h), ctypes.byref(bad), None)
     assert rc == -1 and b"2^a 3^b" in lib.lisa_td_last_error()
+    bad = api.make_config(dt=5.0, n=17280, tdi_nested=2)
+    rc = lib.lisa_td_create(ctypes.byref(h), ctypes.byref(bad), None)
+    assert rc == -1 and b"tdi_nested" in lib.lisa_td_last_error()
     bad = api.make_config(dt=5.0, n=17280, lagrange_order=9)
     assert lib.lisa_td_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
     assert lib.lisa_td_create(None, ctypes.byref(bad), None) == -1
