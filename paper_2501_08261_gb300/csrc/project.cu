@@ -134,11 +134,18 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
 // the tile (a second-order expansion in Omega dt, error < 1e-9 s) and the
 // spacecraft offsets k.rho (FP32 table relative to g) enter only as small
 // FP32 numbers next to exact integers.
+//
+// Lagrange weights: the paired form (lagrange.cuh) for K >= 8, its per-pair
+// constants passed as a kernel parameter (constant bank).  The staged window
+// covers every stencil by construction (halo), so the stencils read shared
+// memory without a bounds branch and can be interleaved; a stencil found
+// outside the window is recomputed through the bounds-checked path.
 template <int K>
-__global__ void __launch_bounds__(256) project_mixed_kernel(
+__global__ void __launch_bounds__(256, 2) project_mixed_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
-    int tile, int halo, int nL, float rL, const int64_t* __restrict__ woff) {
+    int tile, int halo, int nL, float rL, const int64_t* __restrict__ woff,
+    const LagrangePairs pairs) {
   // shared memory: (h+, hx) pairs [rows][32] -- 256-byte rows, so that a
   // 64-bit load of lane w touches banks 2w, 2w+1 whatever row each walker's
   // stencil is on (conflict-free per half-warp) -- then the orbit records
@@ -195,14 +202,21 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
   const float odt = (float)(kOmegaOrb * dt);
   const float2* hw = h + (int64_t)w * n;
   float cinv[K];
+  if constexpr (K < 8) {
 #pragma unroll
-  for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
+    for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
+  }
+  auto weights = [&](float e, float* wts) {
+    if constexpr (K >= 8) lagrange_weights_paired<K>(e, pairs, wts);
+    else lagrange_weights<float, K>(e, cinv, wts);
+  };
 
-  // interpolate h at local row position `row0 + f` (row0 integer, f small)
+  // interpolate h at local row position `row0 + f` (row0 integer, f small),
+  // reading global memory where the stencil leaves the staged window
   auto interp = [&](int row0, float f, float& hp, float& hc) {
     float fl = floorf(f);
     float wts[K];
-    lagrange_weights<float, K>(f - fl, cinv, wts);
+    weights(f - fl, wts);
     int loc = row0 + (int)fl - (K - 2) / 2;
     float sp = 0.0f, sc = 0.0f;
     if (loc >= 0 && loc + K <= rows) {
@@ -232,6 +246,29 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     hc = sc;
   };
 
+  // the same from the staged window only; `bad` records a stencil outside it
+  auto interp_fast = [&](int row0, float f, float& hp, float& hc, bool& bad) {
+    float fl = floorf(f);
+    float wts[K];
+    weights(f - fl, wts);
+    int loc = row0 + (int)fl - (K - 2) / 2;
+    const bool inr = loc >= 0 && loc + K <= rows;
+    bad = bad || !inr;
+    loc = inr ? loc : 0;
+    float sp = 0.0f, sc = 0.0f, sp1 = 0.0f, sc1 = 0.0f;   // two chains each (FMA latency)
+#pragma unroll
+    for (int j = 0; j < K; j += 2) {
+      const float2 v = hws[(loc + j) * 32 + lane];
+      const float2 u = hws[(loc + j + 1) * 32 + lane];
+      sp = fmaf(wts[j], v.x, sp);
+      sc = fmaf(wts[j], v.y, sc);
+      sp1 = fmaf(wts[j + 1], u.x, sp1);
+      sc1 = fmaf(wts[j + 1], u.y, sc1);
+    }
+    hp = sp + sp1;
+    hc = sc + sc1;
+  };
+
   for (int s = warp; s < tile; s += nw) {
     const int64_t i = i0 + s;
     if (i >= n) break;
@@ -240,22 +277,41 @@ __global__ void __launch_bounds__(256) project_mixed_kernel(
     const float dS = d * p1 - 0.5f * d * d * sa;     // k.g(t) - k.g(t_a)
     const float base_f = -fra - dS * idt;
     float hpr[3], hcr[3];
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       float kr = k0 * O.rr[q][0] + k1 * O.rr[q][1] + k2 * O.rr[q][2];
-      interp(s + halo, base_f - kr * idt, hpr[q], hcr[q]);
+      interp_fast(s + halo, base_f - kr * idt, hpr[q], hcr[q], bad);
     }
-#pragma unroll
+    if (bad) {
+#pragma unroll 1
+      for (int q = 0; q < 3; ++q) {
+        float kr = k0 * O.rr[q][0] + k1 * O.rr[q][1] + k2 * O.rr[q][2];
+        float a, b;
+        interp(s + halo, base_f - kr * idt, a, b);
+        if (q == 0) { hpr[0] = a; hcr[0] = b; }
+        else if (q == 1) { hpr[1] = a; hcr[1] = b; }
+        else { hpr[2] = a; hcr[2] = b; }
+      }
+    }
+    // six senders, two per iteration: the fully unrolled nine-stencil body
+    // (~36 KB of code) stalled on instruction fetch
+#pragma unroll 2
     for (int j = 0; j < kNLink; ++j) {
-      const int rq = link_receiver(j);
       float ks = k0 * O.rs[j][0] + k1 * O.rs[j][1] + k2 * O.rs[j][2];
-      float hps_, hcs_;
-      interp(s + halo - nL, base_f - rL - (O.L[j] + ks) * idt, hps_, hcs_);
+      const float fs = base_f - rL - (O.L[j] + ks) * idt;
+      float hs, cs;
+      bool bj = false;
+      interp_fast(s + halo - nL, fs, hs, cs, bj);
+      if (bj) interp(s + halo - nL, fs, hs, cs);
+      const int rq = link_receiver(j);
+      const float hr = rq == 0 ? hpr[0] : (rq == 1 ? hpr[1] : hpr[2]);
+      const float cr = rq == 0 ? hcr[0] : (rq == 1 ? hcr[1] : hcr[2]);
       float nx = O.n[j][0], ny = O.n[j][1], nz = O.n[j][2];
       float un = u0 * nx + u1 * ny + u2 * nz;
       float vn = v0 * nx + v1 * ny + v2 * nz;
       float kn = k0 * nx + k1 * ny + k2 * nz;
-      float val = ((un * un - vn * vn) * (hps_ - hpr[rq]) + 2.0f * un * vn * (hcs_ - hcr[rq])) /
+      float val = ((un * un - vn * vn) * (hs - hr) + 2.0f * un * vn * (cs - cr)) /
                   (2.0f * (1.0f - kn));
       if (w < W && i >= lo) y[((int64_t)j * n + i) * ldw + w] = val;
     }
@@ -292,7 +348,8 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
     dim3 blockm(32, c->tune_warps > 0 ? c->tune_warps : 8);
     project_mixed_kernel<K><<<grid, blockm, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                       c->orb32, (const float2*)h, (float*)y,
-                                                      tile, halo, nL, rL, c->woff);
+                                                      tile, halo, nL, rL, c->woff,
+                                                      lagrange_pairs<K>());
   }
   return cudaGetLastError();
 }
