@@ -141,14 +141,17 @@ struct TdiTable {
 // fraction drifts by j (a1 + j a2) samples (j = i - i_a); m1 = sum (C_f - C)
 // is the first-moment error of the rounding.  The kernel evaluates
 //   y_c + sum_m C_m dy_{c+m} + (j (a1 + j a2) - m1) dy_c.
+// C, m1 and the s* fields carry the term's sign (+-1, exact), so the kernel
+// adds them without multiplying; a1, a2, eps_a stay unsigned for positions.
 constexpr int kTdiTile = 64;
-struct TdiTileTerm {
-  float C[32];           // C[m + H], m = -H .. H (H = (K-2)/2); C[K-1..31] = 0
-  float m1, a1, a2;
+struct alignas(16) TdiTileTerm {
+  float C[32];           // sign * C[m + H], m = -H .. H (H = (K-2)/2); C[K-1..31] = 0
+  float m1, a1, a2;      // sign * m1; drift of the fraction j (a1 + j a2)
   float eps_a;
   int bo;
   int split;             // the fraction leaves [0, 1) inside the tile
-  int pad[2];
+  float sa1, sa2, se;    // sign * a1, sign * a2, sign * eps_a
+  int pad[3];
 };
 
 // ---- small helpers --------------------------------------------------------

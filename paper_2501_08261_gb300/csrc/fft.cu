@@ -130,15 +130,19 @@ template <typename C> struct Dft<7, C> {
 };
 
 // one Stockham stage of radix RAD: A (natural sub-blocks of length L) -> B;
-// tw is the m-point table W_m^j in shared memory
+// tw is the m-point table W_m^j in shared memory.  P = 2^lgP columns; j / L
+// by the multiply-high with magL = floor((2^32 - 1) / L) + 1, exact for
+// j, L < 2^16 (checked by plan_fft), and j itself when L = 1
 template <int RAD, typename C>
-__device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, int P,
-                      const C* __restrict__ tw, int tid, int nth) {
+__device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, unsigned magL,
+                      int lgP, const C* __restrict__ tw, int tid, int nth) {
   const int nb = m / RAD;
   const int stride = m / (L * RAD);
-  for (int item = tid; item < nb * P; item += nth) {
-    const int p = item % P, j = item / P;
-    const int k = j % L;
+  const int P = 1 << lgP;
+  for (int item = tid; item < (nb << lgP); item += nth) {
+    const int p = item & (P - 1), j = item >> lgP;
+    const int jq = L == 1 ? j : (int)__umulhi((unsigned)j, magL);
+    const int k = j - jq * L;
     C a[RAD];
 #pragma unroll
     for (int q = 0; q < RAD; ++q) {
@@ -152,22 +156,23 @@ __device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, 
   }
 }
 
-// full m-point transform of P columns; returns the buffer holding the result
+// full m-point transform of 2^lgP columns; returns the buffer holding the result
 template <typename C>
-__device__ C* transform(C* buf0, C* buf1, int m, int P, const Radices& rd,
+__device__ C* transform(C* buf0, C* buf1, int m, int lgP, const Radices& rd,
                         const C* __restrict__ tw) {
   C* A = buf0;
   C* B = buf1;
   int L = 1;
   for (int s = 0; s < rd.nr; ++s) {
     const int r = rd.r[s];
+    const unsigned mag = L > 1 ? 0xFFFFFFFFu / (unsigned)L + 1u : 0u;
     switch (r) {
-      case 2: stage<2>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
-      case 3: stage<3>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
-      case 4: stage<4>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
-      case 5: stage<5>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
-      case 7: stage<7>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
-      default: stage<8>(A, B, m, L, P, tw, threadIdx.x, blockDim.x); break;
+      case 2: stage<2>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      case 3: stage<3>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      case 4: stage<4>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      case 5: stage<5>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      case 7: stage<7>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      default: stage<8>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
     }
     __syncthreads();
     C* t = A;
@@ -183,12 +188,13 @@ constexpr int kU = 8;   // global loads batched per thread in the staging loops
 template <typename R>
 __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
                                                     typename CT<R>::T* __restrict__ fy, int64_t n,
-                                                    int n1, int n2, int Pt, int Pb, Radices rd,
+                                                    int n1, int n2, int Pt, int lgPb, Radices rd,
                                                     const typename CT<R>::T* __restrict__ tw1,
                                                     const typename CT<R>::T* __restrict__ twn,
                                                     const int* __restrict__ chans,
                                                     int64_t cstride, int ldc) {
   using C = typename CT<R>::T;
+  const int Pb = 1 << lgPb;
   extern __shared__ unsigned char smem_raw[];
   C* b0 = reinterpret_cast<C*>(smem_raw);
   C* b1 = b0 + (size_t)n1 * Pb;
@@ -207,7 +213,7 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
     for (int u = 0; u < kU; ++u) {
       const int item = base + u * blockDim.x;
       if (item < total) {
-        const int a = item / Pb, p = item % Pb;
+        const int a = item >> lgPb, p = item & (Pb - 1);
         v[u] = xc[((int64_t)n2 * a + b) * ldc + pb0 + p];
       }
     }
@@ -218,20 +224,20 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
     }
   }
   __syncthreads();
-  C* res = transform(b0, b1, n1, Pb, rd, (const C*)tws);
+  C* res = transform(b0, b1, n1, lgPb, rd, (const C*)tws);
   C* out = fy + (int64_t)c * n * Pt;
   for (int base = threadIdx.x; base < total; base += blockDim.x * kU) {
     C t[kU];
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int item = base + u * blockDim.x;
-      if (item < total) t[u] = twn[(int64_t)b * (item / Pb)];
+      if (item < total) t[u] = twn[(int64_t)b * (item >> lgPb)];
     }
 #pragma unroll
     for (int u = 0; u < kU; ++u) {
       const int item = base + u * blockDim.x;
       if (item < total) {
-        const int k1 = item / Pb, p = item % Pb;
+        const int k1 = item >> lgPb, p = item & (Pb - 1);
         out[((int64_t)k1 * n2 + b) * Pt + pb0 + p] = cmulv(res[item], t[u]);
       }
     }
@@ -241,11 +247,13 @@ __global__ void __launch_bounds__(512) pass1_kernel(const R* __restrict__ x,
 template <typename R>
 __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __restrict__ fy,
                                                     double* __restrict__ partial, int64_t n,
-                                                    int n1, int n2, int Pt, int Pb, Radices rd,
+                                                    int n1, int n2, int Pt, int lgPb, Radices rd,
                                                     const typename CT<R>::T* __restrict__ tw2,
                                                     const double* __restrict__ psdw,
-                                                    const int* __restrict__ chans) {
+                                                    const int* __restrict__ chans,
+                                                    int64_t klo, int64_t khi) {
   using C = typename CT<R>::T;
+  const int Pb = 1 << lgPb;
   extern __shared__ unsigned char smem_raw[];
   // rows rA and rB side by side: columns [0, Pb) of row rA, [Pb, 2 Pb) of row
   // rB, transformed together (one set of radix stages for both)
@@ -268,7 +276,7 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
     for (int u = 0; u < kU; ++u) {
       const int item = base + u * blockDim.x;
       if (item < total) {
-        const int j = item / Pb, p = item % Pb;
+        const int j = item >> lgPb, p = item & (Pb - 1);
         va[u] = in[((int64_t)rA * n2 + j) * Pt + pb0 + p];
         vc[u] = in[((int64_t)rB * n2 + j) * Pt + pb0 + p];
       }
@@ -277,14 +285,14 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
     for (int u = 0; u < kU; ++u) {
       const int item = base + u * blockDim.x;
       if (item < total) {
-        const int j = item / Pb, p = item % Pb;
+        const int j = item >> lgPb, p = item & (Pb - 1);
         u0[j * P2 + p] = va[u];
         u0[j * P2 + Pb + p] = vc[u];
       }
     }
   }
   __syncthreads();
-  const C* X = transform(u0, u1, n2, P2, rd, (const C*)tws);
+  const C* X = transform(u0, u1, n2, lgPb + 1, rd, (const C*)tws);
   const int64_t nb = n / 2 + 1;
   const double* wv = psdw + (c == 2 ? nb : 0);
   // walker 2p, 2p+1 (p fixed per thread).  FP64 transforms accumulate in FP64.
@@ -296,16 +304,16 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   float faccx = 0.0f, faccy = 0.0f;
   const int nrow = single ? 1 : 2;
   for (int item = threadIdx.x; item < n2 * Pb; item += blockDim.x) {
-    const int k2 = item / Pb, p = item % Pb;
+    const int k2 = item >> lgPb, p = item & (Pb - 1);
     for (int rr = 0; rr < nrow; ++rr) {
       const int co = rr == 0 ? 0 : Pb;             // this row's columns
       const int cm = single ? 0 : Pb - co;         // its mirror row's columns
       const int row = rr == 0 ? rA : rB;
       const int64_t k = row + (int64_t)n1 * k2;
-      if (k >= nb) continue;
+      if (k >= nb || k < klo || k > khi) continue;   // outside a safe superset of the band
       const double wk = wv[k];
       if (wk == 0.0) continue;
-      const int km = (single && row == 0) ? (n2 - k2) % n2 : n2 - 1 - k2;
+      const int km = (single && row == 0) ? (k2 == 0 ? 0 : n2 - k2) : n2 - 1 - k2;
       C z = X[k2 * P2 + co + p];
       C zm = X[km * P2 + cm + p];
       if constexpr (sizeof(R) == 4) {
@@ -398,6 +406,10 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
   if (c->tune_pb1 > 0 && pb_fits(p.n1, 2, sizeof(C), Pt, c->tune_pb1)) pb1 = c->tune_pb1;
   if (c->tune_pb2 > 0 && pb_fits(p.n2, 4, sizeof(C), Pt, c->tune_pb2)) pb2 = c->tune_pb2;
   if (pb1 == 0 || pb2 == 0) return cudaErrorInvalidValue;
+  int lg1 = 0, lg2 = 0;
+  while ((1 << lg1) < pb1) ++lg1;
+  while ((1 << lg2) < pb2) ++lg2;
+  if ((1 << lg1) != pb1 || (1 << lg2) != pb2) return cudaErrorInvalidValue;
   size_t sm1 = ((size_t)2 * pb1 + 1) * p.n1 * sizeof(C);
   size_t sm2 = ((size_t)4 * pb2 + 1) * p.n2 * sizeof(C);
   cudaFuncSetAttribute(pass1_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
@@ -415,12 +427,17 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
       cstride = c->fft_cstride;
       ldc = c->fft_ldr / 2;
     }
-    pass1_kernel<R><<<g1, 512, sm1, s>>>(x, (C*)c->fy, c->n, p.n1, p.n2, Pt, pb1, r1,
+    pass1_kernel<R><<<g1, 512, sm1, s>>>(x, (C*)c->fy, c->n, p.n1, p.n2, Pt, lg1, r1,
                                          (const C*)p.tw1, (const C*)p.tw_n, chans, cstride, ldc);
   } else {
     dim3 g2((unsigned)(p.n1 / 2 + 1), (unsigned)(Pt / pb2), (unsigned)nch);
+    // bins outside [klo, khi] have zero weight: a superset of the band by one
+    // bin on each side (the weights themselves still decide inside it)
+    const double df = 1.0 / ((double)c->n * c->cfg.dt);
+    int64_t klo = (int64_t)floor(c->cfg.f_lo / df) - 1, khi = (int64_t)ceil(c->cfg.f_hi / df) + 1;
+    if (klo < 0) klo = 0;
     pass2_kernel<R><<<g2, 512, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
-                                         pb2, r2, (const C*)p.tw2, c->psdw, chans);
+                                         lg2, r2, (const C*)p.tw2, c->psdw, chans, klo, khi);
   }
   return cudaGetLastError();
 }
@@ -435,6 +452,7 @@ int plan_fft(int64_t n, FftPlan* p) {
   int64_t best = 1;
   for (int64_t d = 1; d * d <= n; ++d)
     if (n % d == 0) best = d;
+  if (n / best >= (1 << 16)) return -1;   // the stage index arithmetic needs m < 2^16
   p->n1 = (int)best;
   p->n2 = (int)(n / best);
   Radices a, b;

@@ -304,8 +304,14 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
       mom += (double)cf - c;
     }
   }
-  R.m1 = (float)mom;
-  R.pad[0] = R.pad[1] = 0;
+  // the term's sign, exact on every field that the kernel only adds
+  const float sg = (float)T.sign;
+  for (int q = 0; q < 32; ++q) R.C[q] *= sg;
+  R.m1 = sg * (float)mom;
+  R.sa1 = sg * R.a1;
+  R.sa2 = sg * R.a2;
+  R.se = sg * R.eps_a;
+  R.pad[0] = R.pad[1] = R.pad[2] = 0;
   out[id] = R;
 }
 
@@ -352,20 +358,20 @@ __device__ __forceinline__ void add_rows(f2 (&hi)[SPT], f2 (&lo)[SPT], const flo
 }
 
 // small[r] += sum_{m'} c[m'] dy[b0 + r + m'] + dr_r dy[b0 + r + H], c and dr carrying the
-// sign; the linear-interpolation part sg eps_a dy[b0 + r + H] is added to the main
-// accumulator exactly (FMA two-product, two-sum), since its rounding in the small
-// accumulator is noise of size ulp(|dy|) that TDI 2's T channel no longer suppresses
+// sign (stored signed in the tile table); the linear-interpolation part sg eps_a
+// dy[b0 + r + H] is added to the main accumulator exactly (FMA two-product,
+// two-sum), since its rounding in the small accumulator is noise of size
+// ulp(|dy|) that TDI 2's T channel no longer suppresses
 template <int K, int SPT>
 __device__ __forceinline__ void apply_tile_term(f2 (&main)[SPT], f2 (&acc)[SPT],
                                                 const float2* __restrict__ dyw,
-                                                const TdiTileTerm& P, float sg, int s0, int b0,
-                                                int lane) {
+                                                const TdiTileTerm& P, int s0, int b0, int lane) {
   constexpr int H = (K - 2) / 2;
   constexpr int NT = K - 1;                       // taps on the differences
   float c[NT];
 #pragma unroll
-  for (int k = 0; k < NT; ++k) c[k] = sg * P.C[k];
-  const float m1 = P.m1, a1 = P.a1, a2 = P.a2, se = sg * P.eps_a;
+  for (int k = 0; k < NT; ++k) c[k] = P.C[k];
+  const float m1 = P.m1, a1 = P.sa1, a2 = P.sa2, se = P.se;
   f2 win[SPT];
 #pragma unroll
   for (int r = 0; r < SPT; ++r) win[r] = ld2(&dyw[(b0 + r) * kPW2 + lane]);
@@ -380,7 +386,7 @@ __device__ __forceinline__ void apply_tile_term(f2 (&main)[SPT], f2 (&acc)[SPT],
 #pragma unroll
       for (int r = 0; r < SPT; ++r) {
         const float jj = (float)(s0 + r);
-        const float dr = sg * (jj * fmaf(jj, a2, a1) - m1);
+        const float dr = jj * fmaf(jj, a2, a1) - m1;
         acc[r].x = fmaf(dr, win[r].x, acc[r].x);
         acc[r].y = fmaf(dr, win[r].y, acc[r].y);
         const float px = se * win[r].x, py = se * win[r].y;
@@ -510,13 +516,13 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
         const int b0 = c0 - (K - 2) / 2;
         if (T.chan == 0) {
           add_rows<SPT>(mx, sx, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(mx, sx, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(mx, sx, dyw, P, s0, b0, lane);
         } else if (T.chan == 1) {
           add_rows<SPT>(my, sy, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(my, sy, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(my, sy, dyw, P, s0, b0, lane);
         } else {
           add_rows<SPT>(mz, sz, yw, c0, sg, lane);
-          apply_tile_term<K, SPT>(mz, sz, dyw, P, sg, s0, b0, lane);
+          apply_tile_term<K, SPT>(mz, sz, dyw, P, s0, b0, lane);
         }
       } else {
 #pragma unroll
