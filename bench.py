@@ -390,7 +390,8 @@ def run_ours(args):
         "stage_ms": {k: round(v, 4) for k, v in per_call.items()},
         "gpu_launches": 7 * args.steps,
         "autotune": {"project_tile": tuned[0], "project_warps": tuned[1], "fft_pass1_pb": tuned[2],
-                     "fft_pass2_pb": tuned[3]},
+                     "fft_pass2_pb": tuned[3], "fft_pass1_threads": tuned[4],
+                     "fft_pass2_threads": tuned[5]},
         "roofline": roof,
         "clocks": clk,
         "e2e": {"value": round(evals * args.steps / (ms_e2e * 1e-3), 2), "unit": "logL evals/s",

@@ -141,13 +141,14 @@ int lisa_td_ragged_graph(lisa_td_ctx* ctx, int32_t enable);
 /* Autotuner (measurement support, no paper counterpart): times the launch
  * shapes that are free parameters of the path on the caller's walkers
  * params_dev [W][15] -- the projection's tile length (64, 128, 256 samples
- * per CTA) and warps per CTA (4, 8; mixed path), and the columns per block of
- * the two FFT passes -- and keeps the fastest in the context; with n_host
- * [W] (window lengths as for lisa_td_loglike_ragged, may be NULL) also the
- * FFT columns per block of each window length.  Results are unchanged up to
- * rounding (the projection's FP32 tile anchors move with the tile length);
- * the Lagrange order is not tuned (it changes the result).  choice_host [4]
- * (may be NULL): tile, warps, pass-1 and pass-2 columns per block chosen.
+ * per CTA) and warps per CTA (4, 8; mixed path), and the columns per block
+ * (1..16) and threads per block (256, 512) of the two FFT passes -- and keeps
+ * the fastest in the context; with n_host [W] (window lengths as for
+ * lisa_td_loglike_ragged, may be NULL) also the FFT shapes of each window
+ * length.  Results are unchanged up to rounding (the projection's FP32 tile
+ * anchors move with the tile length); the Lagrange order is not tuned (it
+ * changes the result).  choice_host [6] (may be NULL): tile, warps, pass-1 and
+ * pass-2 columns per block, pass-1 and pass-2 threads per block.
  * Uses the context's workspace and synchronises `stream`; call it before
  * timing or capturing. */
 int lisa_td_autotune(lisa_td_ctx* ctx, const double* params_dev, int32_t W,

@@ -165,9 +165,10 @@ def lisa_td_loglike_ragged(ctx, params, W, n_per_walker, logl, status=None, stre
 
 
 def lisa_td_autotune(ctx, params, W, n_per_walker=None, stream=None):
-    """-> (tile, warps, pass-1 pb, pass-2 pb) chosen and kept by the context."""
+    """-> (tile, warps, pass-1 pb, pass-2 pb, pass-1 threads, pass-2 threads)
+    chosen and kept by the context."""
     import numpy as np
-    ch = (ctypes.c_int32 * 4)()
+    ch = (ctypes.c_int32 * 6)()
     if n_per_walker is None:
         nh = None
     else:

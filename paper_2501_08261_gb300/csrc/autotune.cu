@@ -1,7 +1,7 @@
 // lisa_td_autotune: measured choice of the launch shapes that are free
 // parameters of the path -- the projection's tile length (samples per CTA)
-// and warps per CTA, and the columns per block of the two FFT passes (for the
-// whole grid and, for ragged batches, for each window length).  Every
+// and warps per CTA, and the columns and threads per block of the two FFT
+// passes (for the whole grid and, for ragged batches, for each window length).  Every
 // candidate computes the same result up to rounding (the projection's FP32
 // tile anchors move with the tile length); the Lagrange order is not a
 // candidate, since it changes the interpolation and therefore the result.
@@ -45,28 +45,39 @@ float time_it(F f, cudaStream_t s) {
   return ms;
 }
 
-// pass 1 / pass 2 columns per block for context (or view) v and Wp columns
+// pass 1 / pass 2 columns per block and threads per block for context (or
+// view) v and Wp columns
 void tune_fft(lisa_td_ctx* v, int Wp, const void* r, cudaStream_t s) {
   const int cand[] = {1, 2, 4, 8, 16};
+  const int bsz[] = {256, 512};
   float best = FLT_MAX;
-  int pick = 0;
-  for (int pb : cand) {
-    if (!fft_pb_valid(v, Wp, 1, pb)) continue;
-    v->tune_pb1 = pb;
-    float ms = time_it([&] { return launch_fft_pass1(v, Wp, r, s); }, s);
-    if (ms < best) { best = ms; pick = pb; }
+  int pick = 0, pbs = 512;
+  for (int bs : bsz) {
+    for (int pb : cand) {
+      if (!fft_pb_valid(v, Wp, 1, pb)) continue;
+      v->tune_pb1 = pb;
+      v->tune_bs1 = bs;
+      float ms = time_it([&] { return launch_fft_pass1(v, Wp, r, s); }, s);
+      if (ms < best) { best = ms; pick = pb; pbs = bs; }
+    }
   }
   v->tune_pb1 = pick;
+  v->tune_bs1 = pbs;
   launch_fft_pass1(v, Wp, r, s);
   best = FLT_MAX;
   pick = 0;
-  for (int pb : cand) {
-    if (!fft_pb_valid(v, Wp, 2, pb)) continue;
-    v->tune_pb2 = pb;
-    float ms = time_it([&] { return launch_fft_pass2(v, Wp, s); }, s);
-    if (ms < best) { best = ms; pick = pb; }
+  pbs = 512;
+  for (int bs : bsz) {
+    for (int pb : cand) {
+      if (!fft_pb_valid(v, Wp, 2, pb)) continue;
+      v->tune_pb2 = pb;
+      v->tune_bs2 = bs;
+      float ms = time_it([&] { return launch_fft_pass2(v, Wp, s); }, s);
+      if (ms < best) { best = ms; pick = pb; pbs = bs; }
+    }
   }
   v->tune_pb2 = pick;
+  v->tune_bs2 = pbs;
 }
 
 }  // namespace
@@ -119,6 +130,8 @@ extern "C" int lisa_td_autotune(lisa_td_ctx* c, const double* params_dev, int32_
       tune_fft(&f, kv.second + (kv.second & 1), c->r, s);
       v->tune_pb1 = f.tune_pb1;
       v->tune_pb2 = f.tune_pb2;
+      v->tune_bs1 = f.tune_bs1;
+      v->tune_bs2 = f.tune_bs2;
     }
   }
   e = cudaStreamSynchronize(s);
@@ -128,6 +141,8 @@ extern "C" int lisa_td_autotune(lisa_td_ctx* c, const double* params_dev, int32_
     choice_host[1] = c->tune_warps;
     choice_host[2] = c->tune_pb1;
     choice_host[3] = c->tune_pb2;
+    choice_host[4] = c->tune_bs1;
+    choice_host[5] = c->tune_bs2;
   }
   return LISA_TD_OK;
 }

@@ -405,6 +405,8 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
   int pb2 = pick_pb(p.n2, 4, sizeof(C), Pt);
   if (c->tune_pb1 > 0 && pb_fits(p.n1, 2, sizeof(C), Pt, c->tune_pb1)) pb1 = c->tune_pb1;
   if (c->tune_pb2 > 0 && pb_fits(p.n2, 4, sizeof(C), Pt, c->tune_pb2)) pb2 = c->tune_pb2;
+  const int bs1 = c->tune_bs1 == 256 ? 256 : 512;   // threads per block (a multiple of pb)
+  const int bs2 = c->tune_bs2 == 256 ? 256 : 512;
   if (pb1 == 0 || pb2 == 0) return cudaErrorInvalidValue;
   int lg1 = 0, lg2 = 0;
   while ((1 << lg1) < pb1) ++lg1;
@@ -427,7 +429,7 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
       cstride = c->fft_cstride;
       ldc = c->fft_ldr / 2;
     }
-    pass1_kernel<R><<<g1, 512, sm1, s>>>(x, (C*)c->fy, c->n, p.n1, p.n2, Pt, lg1, r1,
+    pass1_kernel<R><<<g1, bs1, sm1, s>>>(x, (C*)c->fy, c->n, p.n1, p.n2, Pt, lg1, r1,
                                          (const C*)p.tw1, (const C*)p.tw_n, chans, cstride, ldc);
   } else {
     dim3 g2((unsigned)(p.n1 / 2 + 1), (unsigned)(Pt / pb2), (unsigned)nch);
@@ -436,7 +438,7 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
     const double df = 1.0 / ((double)c->n * c->cfg.dt);
     int64_t klo = (int64_t)floor(c->cfg.f_lo / df) - 1, khi = (int64_t)ceil(c->cfg.f_hi / df) + 1;
     if (klo < 0) klo = 0;
-    pass2_kernel<R><<<g2, 512, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
+    pass2_kernel<R><<<g2, bs2, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
                                          lg2, r2, (const C*)p.tw2, c->psdw, chans, klo, khi);
   }
   return cudaGetLastError();

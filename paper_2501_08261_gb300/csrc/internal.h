@@ -70,6 +70,7 @@ struct lisa_td_ctx {
   // the projection (samples per CTA) and its warps per CTA; columns per block
   // of FFT pass 1 and pass 2
   int tune_tile, tune_warps, tune_pb1, tune_pb2;
+  int tune_bs1, tune_bs2;          // FFT threads per block (0: 512)
 };
 
 namespace lisa {

@@ -316,7 +316,7 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
 }
 
 constexpr int kMixTile = kTdiTile;
-constexpr int kMixSpt = 8;                  // samples per thread (8 warps x 8 = 64)
+constexpr int kMixSpt = 4;                  // samples per thread (16 warps x 4 = 64)
 constexpr int kMixWarps = kMixTile / kMixSpt;
 constexpr int kPW2 = 33;                    // padded walker pairs per row
 
@@ -434,7 +434,7 @@ __device__ __noinline__ float4 split_one(const float2* __restrict__ yw, const Td
   return make_float4(yc.x, yc.y, ax, ay);
 }
 
-// One CTA = 64 walkers (two per lane) x 64 output samples (8 warps x 8).
+// One CTA = 64 walkers (two per lane) x 64 output samples (16 warps x 4).
 // Accumulators: `m*` hold the |y|-sized centre samples of every term
 // (compensated), `s*` the difference FIRs, corrections and compensation terms;
 // A, E, T are formed from the m parts error-free before the s parts are added.

@@ -34,6 +34,7 @@ def test_autotune_keeps_the_likelihood(precision):
     choice = api.lisa_td_autotune(tuned.ctx, _t(th), W, windows)
     assert choice[0] in (64, 128, 256) and choice[2] in (1, 2, 4, 8, 16) and choice[3] in (1, 2, 4, 8, 16)
     assert choice[1] == (0 if precision == 0 else choice[1]) and (precision == 0 or choice[1] in (4, 8))
+    assert choice[4] in (256, 512) and choice[5] in (256, 512)
     a, b = plain.loglike(_t(th)).cpu().numpy(), tuned.loglike(_t(th)).cpu().numpy()
     ra = plain.loglike_ragged(_t(th), windows).cpu().numpy()
     rb = tuned.loglike_ragged(_t(th), windows).cpu().numpy()
