@@ -138,7 +138,7 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
   struct { void** p; size_t bytes; } allocs[] = {
       {(void**)&c->orb64, sizeof(lisa::OrbitRec64) * n},
       {(void**)&c->orb32, sizeof(lisa::OrbitRec32) * n},
-      {(void**)&c->psdw, sizeof(double) * 2 * (n / 2 + 1)},
+      {(void**)&c->psdw, lisa::psd_bytes(n)},
       {(void**)&c->plan.tw_n, cs * n},
       {(void**)&c->plan.tw1, cs * c->plan.n1},
       {(void**)&c->plan.tw2, cs * c->plan.n2},

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
                                                     const typename CT<R>::T* __restrict__ tw2,
                                                     const double* __restrict__ psdw,
                                                     const int* __restrict__ chans,
-                                                    int64_t klo, int64_t khi) {
+                                                    int klo, int khi) {
   using C = typename CT<R>::T;
   const int Pb = 1 << lgPb;
   extern __shared__ unsigned char smem_raw[];
@@ -293,8 +293,10 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   }
   __syncthreads();
   const C* X = transform(u0, u1, n2, lgPb + 1, rd, (const C*)tws);
-  const int64_t nb = n / 2 + 1;
+  const int nb = (int)(n / 2 + 1);               // n <= 2^24: bin indices fit int
   const double* wv = psdw + (c == 2 ? nb : 0);
+  // FP32 path: the same weights as float x 2^-160, stored after the FP64 ones
+  const float* wv32 = reinterpret_cast<const float*>(psdw + 2 * (int64_t)nb) + (c == 2 ? nb : 0);
   // walker 2p, 2p+1 (p fixed per thread).  FP64 transforms accumulate in FP64.
   // FP32 transforms accumulate in FP32 with exact power-of-two scalings: the
   // weights 4 df dt^2 / S reach 1e47 (x 2^-160: <= 1) and the spectra of
@@ -309,15 +311,14 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
       const int co = rr == 0 ? 0 : Pb;             // this row's columns
       const int cm = single ? 0 : Pb - co;         // its mirror row's columns
       const int row = rr == 0 ? rA : rB;
-      const int64_t k = row + (int64_t)n1 * k2;
+      const int k = row + n1 * k2;
       if (k >= nb || k < klo || k > khi) continue;   // outside a safe superset of the band
-      const double wk = wv[k];
-      if (wk == 0.0) continue;
       const int km = (single && row == 0) ? (k2 == 0 ? 0 : n2 - k2) : n2 - 1 - k2;
-      C z = X[k2 * P2 + co + p];
-      C zm = X[km * P2 + cm + p];
       if constexpr (sizeof(R) == 4) {
-        const float ws = (float)(wk * 0x1p-160);
+        const float ws = wv32[k];
+        if (ws == 0.0f) continue;
+        const C z = X[k2 * P2 + co + p];
+        const C zm = X[km * P2 + cm + p];
         const float zx = z.x * 0x1p64f, zy = z.y * 0x1p64f;
         const float mx = zm.x * 0x1p64f, my = zm.y * 0x1p64f;
         const float xr = 0.5f * (zx + mx), xi = 0.5f * (zy - my);
@@ -325,6 +326,10 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
         faccx = fmaf(ws, fmaf(xr, xr, xi * xi), faccx);
         faccy = fmaf(ws, fmaf(yr, yr, yi * yi), faccy);
       } else {
+        const double wk = wv[k];
+        if (wk == 0.0) continue;
+        const C z = X[k2 * P2 + co + p];
+        const C zm = X[km * P2 + cm + p];
         const double xr = 0.5 * ((double)z.x + (double)zm.x), xi = 0.5 * ((double)z.y - (double)zm.y);
         const double yr = 0.5 * ((double)z.y + (double)zm.y), yi = -0.5 * ((double)z.x - (double)zm.x);
         accx += wk * (xr * xr + xi * xi);
@@ -436,8 +441,9 @@ cudaError_t launch_t(const lisa_td_ctx* c, int Wpad, const void* r, int pass, cu
     // bins outside [klo, khi] have zero weight: a superset of the band by one
     // bin on each side (the weights themselves still decide inside it)
     const double df = 1.0 / ((double)c->n * c->cfg.dt);
-    int64_t klo = (int64_t)floor(c->cfg.f_lo / df) - 1, khi = (int64_t)ceil(c->cfg.f_hi / df) + 1;
-    if (klo < 0) klo = 0;
+    double flo = floor(c->cfg.f_lo / df) - 1.0, fhi = ceil(c->cfg.f_hi / df) + 1.0;
+    const int klo = flo < 0.0 ? 0 : (int)flo;
+    const int khi = fhi > (double)c->n ? (int)c->n : (int)fhi;
     pass2_kernel<R><<<g2, bs2, sm2, s>>>((const C*)c->fy, c->partial, c->n, p.n1, p.n2, Pt,
                                          lg2, r2, (const C*)p.tw2, c->psdw, chans, klo, khi);
   }

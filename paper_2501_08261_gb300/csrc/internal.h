@@ -29,7 +29,8 @@ struct lisa_td_ctx {
   int esize;                       // 8 (FP64) or 4 (mixed)
   lisa::OrbitRec64* orb64;
   lisa::OrbitRec32* orb32;
-  double* psdw;                    // [2][n/2+1]: dt^2 * 4 df / S (AE, T) in band, else 0
+  double* psdw;                    // [2][n/2+1]: dt^2 * 4 df / S (AE, T) in band, else 0,
+                                   // followed by the same as float x 2^-160 (psd_bytes)
   lisa::FftPlan plan;
   lisa::TdiTable* tdi_tab;         // device copy of the TDI term table
   int tdi_nd;                      // most light times in one delay
@@ -81,6 +82,9 @@ cudaError_t launch_prep(const lisa_td_ctx* c, const double* params, int W, int W
 // orbit.cu (create-time tables)
 cudaError_t launch_orbit_tables(const lisa_td_ctx* c, cudaStream_t s);
 cudaError_t launch_psd_weights(const lisa_td_ctx* c, cudaStream_t s);
+// bytes of the psdw block for n samples: FP64 weights, then their FP32 copies
+// scaled by 2^-160 (the mixed pass 2 reads those, with no FP64 arithmetic)
+inline size_t psd_bytes(int64_t n) { return (sizeof(double) + sizeof(float)) * 2 * (size_t)(n / 2 + 1); }
 cudaError_t launch_twiddles(const lisa_td_ctx* c, cudaStream_t s);
 cudaError_t launch_data_copy(const lisa_td_ctx* c, const double* aet, cudaStream_t s);
 // waveform.cu: h[w][i][2] for w < W (row stride n)

@@ -81,7 +81,7 @@ extern "C" int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const
   const size_t cs = 2 * (size_t)c.esize;
   // scratch layout, each region 256-byte aligned
   size_t off[8], at = 0;
-  const size_t bytes[8] = {cs * n, cs * c.plan.n1, cs * c.plan.n2, sizeof(double) * 2 * (n / 2 + 1),
+  const size_t bytes[8] = {cs * n, cs * c.plan.n1, cs * c.plan.n2, psd_bytes(n),
                            sizeof(int) * 4, sizeof(WalkerRec) * (size_t)W,
                            (size_t)c.esize * 3 * n * W,
                            sizeof(double) * 3 * (c.plan.n1 / 2 + 1) * (size_t)W};

@@ -102,6 +102,7 @@ __global__ void orbit_kernel(int64_t n, double t0, double dt, int kind, OrbitRec
 // x = 2 pi f L / c, A_acc = 2.4e-15; TDI 2: times 4 sin^2 2x).
 __global__ void psd_kernel(int64_t nb, int64_t n, double dt, double flo, double fhi, int gen,
                            double* w) {
+  float* w32 = reinterpret_cast<float*>(w + 2 * nb);      // x 2^-160, see psd_bytes
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nb) return;
   double f = (double)k / ((double)n * dt);
@@ -128,6 +129,8 @@ __global__ void psd_kernel(int64_t nb, int64_t n, double dt, double flo, double 
   }
   w[k] = wae;
   w[nb + k] = wt;
+  w32[k] = (float)(wae * 0x1p-160);
+  w32[nb + k] = (float)(wt * 0x1p-160);
 }
 
 template <typename C>

@@ -203,7 +203,7 @@ cudaError_t get_view(lisa_td_ctx* c, Ragged* r, int64_t nv, cudaStream_t s, View
     cudaError_t e = cudaMalloc(&v.plan.tw_n, cs * nv);
     if (e == cudaSuccess) e = cudaMalloc(&v.plan.tw1, cs * v.plan.n1);
     if (e == cudaSuccess) e = cudaMalloc(&v.plan.tw2, cs * v.plan.n2);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&v.psdw, sizeof(double) * 2 * (nv / 2 + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&v.psdw, psd_bytes(nv));
     if (e == cudaSuccess) e = cudaMalloc((void**)&v.data64, sizeof(double) * 3 * nv);
     if (e == cudaSuccess) e = cudaMalloc((void**)&v.data32, sizeof(float) * 3 * nv);
     if (e == cudaSuccess)
