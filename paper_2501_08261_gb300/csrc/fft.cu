@@ -90,43 +90,71 @@ template <typename C> struct Dft<3, C> {
     a[2] = csub(m, v);
   }
 };
-// R = 5, 7: direct sums with the cosines / sines of 2 pi q / R
-template <int R, typename C> struct DftGeneric {
-  __device__ __forceinline__ static void run(C* a, const double* cs, const double* sn) {
-    using T = decltype(a[0].x);
-    C b[R];
+// R = 5, 7: the symmetric form.  With W = exp(-2 pi i / R), pairs q, R - q
+// combine as t_q = a_q + a_{R-q}, u_q = a_q - a_{R-q}, and
+//   X_s = a_0 + sum_q t_q cos(2 pi q s / R) - i sum_q u_q sin(2 pi q s / R),
+//   X_{R-s} = the same with +i,  q, s = 1 .. (R-1)/2.
+// The cosines and sines are compile-time constants of the element type (a
+// __constant__ FP64 table would cost an FP64 conversion per use on the FP32
+// path, and GB300's FP64 pipe runs at 1/64 of FP32).
+template <int R, typename C> struct DftSym {
+  template <typename T>
+  __device__ __forceinline__ static void run(C* a, const T (&cs)[(R - 1) / 2][(R - 1) / 2],
+                                             const T (&sn)[(R - 1) / 2][(R - 1) / 2]) {
+    constexpr int M = (R - 1) / 2;
+    C t[M], u[M];
 #pragma unroll
-    for (int s = 0; s < R; ++s) {
-      T re = a[0].x, im = a[0].y;
-#pragma unroll
-      for (int q = 1; q < R; ++q) {
-        const int k = (q * s) % R;
-        const T c = (T)cs[k], sv = (T)sn[k];     // W^k = c - i sv
-        re += a[q].x * c + a[q].y * sv;
-        im += a[q].y * c - a[q].x * sv;
-      }
-      b[s].x = re;
-      b[s].y = im;
+    for (int q = 0; q < M; ++q) {
+      t[q] = cadd(a[q + 1], a[R - 1 - q]);
+      u[q] = csub(a[q + 1], a[R - 1 - q]);
     }
+    C x0 = a[0];
 #pragma unroll
-    for (int s = 0; s < R; ++s) a[s] = b[s];
+    for (int q = 0; q < M; ++q) x0 = cadd(x0, t[q]);
+#pragma unroll
+    for (int s = 0; s < M; ++s) {
+      C b = a[0], d;
+      d.x = (T)0;
+      d.y = (T)0;
+#pragma unroll
+      for (int q = 0; q < M; ++q) {
+        b.x += cs[s][q] * t[q].x;
+        b.y += cs[s][q] * t[q].y;
+        d.x += sn[s][q] * u[q].x;
+        d.y += sn[s][q] * u[q].y;
+      }
+      // -i d = (d.y, -d.x)
+      a[s + 1].x = b.x + d.y;
+      a[s + 1].y = b.y - d.x;
+      a[R - 1 - s].x = b.x - d.y;
+      a[R - 1 - s].y = b.y + d.x;
+    }
+    a[0] = x0;
   }
 };
-__constant__ double c_cos5[5] = {1.0, 0.30901699437494742, -0.80901699437494742,
-                                 -0.80901699437494742, 0.30901699437494742};
-__constant__ double c_sin5[5] = {0.0, 0.95105651629515357, 0.58778525229247313,
-                                 -0.58778525229247313, -0.95105651629515357};
-__constant__ double c_cos7[7] = {1.0, 0.62348980185873353, -0.22252093395631440,
-                                 -0.90096886790241913, -0.90096886790241913,
-                                 -0.22252093395631440, 0.62348980185873353};
-__constant__ double c_sin7[7] = {0.0, 0.78183148246802981, 0.97492791218182361,
-                                 0.43388373911755812, -0.43388373911755812,
-                                 -0.97492791218182361, -0.78183148246802981};
 template <typename C> struct Dft<5, C> {
-  __device__ __forceinline__ static void run(C* a) { DftGeneric<5, C>::run(a, c_cos5, c_sin5); }
+  __device__ __forceinline__ static void run(C* a) {
+    using T = decltype(a[0].x);
+    // cos / sin (2 pi q s / 5), s, q = 1, 2
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+    const T cs[2][2] = {{c1, c2}, {c2, c1}};
+    const T sn[2][2] = {{s1, s2}, {s2, -s1}};
+    DftSym<5, C>::run(a, cs, sn);
+  }
 };
 template <typename C> struct Dft<7, C> {
-  __device__ __forceinline__ static void run(C* a) { DftGeneric<7, C>::run(a, c_cos7, c_sin7); }
+  __device__ __forceinline__ static void run(C* a) {
+    using T = decltype(a[0].x);
+    // cos / sin (2 pi k / 7), k = 1, 2, 3; entries at k = q s mod 7 (sin odd)
+    const T c1 = (T)0.62348980185873353053, c2 = (T)-0.22252093395631440429,
+            c3 = (T)-0.90096886790241912624;
+    const T s1 = (T)0.78183148246802980871, s2 = (T)0.97492791218182360702,
+            s3 = (T)0.43388373911755812048;
+    const T cs[3][3] = {{c1, c2, c3}, {c2, c3, c1}, {c3, c1, c2}};
+    const T sn[3][3] = {{s1, s2, s3}, {s2, -s3, -s1}, {s3, -s1, s2}};
+    DftSym<7, C>::run(a, cs, sn);
+  }
 };
 
 // one Stockham stage of radix RAD: A (natural sub-blocks of length L) -> B;

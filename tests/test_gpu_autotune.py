@@ -29,6 +29,14 @@ def test_autotune_keeps_the_likelihood(precision):
     plain = api.Likelihood(precision=precision, max_walkers=W + 32, **gpu_kwargs(cfg))
     tuned = api.Likelihood(precision=precision, max_walkers=W + 32, **gpu_kwargs(cfg))
     d = plain.tdi(plain.project(_t(th[:1])))[:, :, 0].to(torch.float64).contiguous()
+    # the mixed path's |dlogL| <= 0.05 holds at SNR 2000 (louder injections
+    # move the truth walker's logL by rounding alone, ~ SNR^2): scale to it
+    plain.set_data(d)
+    far0 = th[:1].copy()
+    far0[0, 8] = 1e30
+    rho = float(np.sqrt(-2.0 * plain.loglike(_t(far0)).cpu().numpy()[0]))
+    d = (d * (2000.0 / rho)).contiguous()
+    th[0, 8] *= rho / 2000.0
     plain.set_data(d)
     tuned.set_data(d)
     choice = api.lisa_td_autotune(tuned.ctx, _t(th), W, windows)
