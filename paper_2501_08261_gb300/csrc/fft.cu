@@ -369,15 +369,19 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
     accx = (double)faccx * 0x1p32;
     accy = (double)faccy * 0x1p32;
   }
-  // per-column reduction: thread t always served column t % Pb (blockDim % Pb == 0)
-  const int p = threadIdx.x % Pb;
+  // per-column reduction in FP64: thread t served column t % Pb (Pb <= 16
+  // divides 32); lanes of a warp with the same column combine by shuffles,
+  // then the warps' sums add in a fixed order (deterministic)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int half = 0; half < 2; ++half) {
-    red[threadIdx.x] = half == 0 ? accx : accy;
+    double v = half == 0 ? accx : accy;
+    for (int off = 16; off >= Pb; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane < Pb) red[wid * Pb + lane] = v;
     __syncthreads();
     if (threadIdx.x < Pb) {
-      double s = 0.0;
-      for (int t = threadIdx.x; t < (int)blockDim.x; t += Pb) s += red[t];
-      partial[((int64_t)c * (n1 / 2 + 1) + rp) * (2 * Pt) + 2 * (pb0 + p) + half] = s;
+      double sum = 0.0;
+      for (int q = 0; q < nwarp; ++q) sum += red[q * Pb + threadIdx.x];
+      partial[((int64_t)c * (n1 / 2 + 1) + rp) * (2 * Pt) + 2 * (pb0 + threadIdx.x) + half] = sum;
     }
     __syncthreads();
   }
