@@ -37,7 +37,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5
 # capture of 30 d x 64 walkers (profiles/tdi_mixed_kernel_30d_64w.md,
 # profiles/project_mixed_kernel_30d_64w.md); traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
-NCU_BYTES_PER_UNIT = {"tdi": 1221.693952e6 / (518400 * 64),
+NCU_BYTES_PER_UNIT = {"tdi": 1228.392704e6 / (518400 * 64),
                       "project": 1216.544000e6 / (518400 * 64)}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 

@@ -15,7 +15,7 @@
 namespace lisa {
 namespace {
 
-constexpr int kReps = 3;
+constexpr int kReps = 5;
 
 // mean milliseconds of `reps` runs of f on stream s (after one untimed run);
 // FLT_MAX if a launch fails (an invalid candidate)
