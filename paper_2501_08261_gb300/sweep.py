@@ -4,7 +4,8 @@ spin model x orbit x precision), printed as a markdown table.
     python -m paper_2501_08261_gb300.sweep [--quick]
 
 Each point creates a context, injects the first walker's response as
-zero-noise data, runs 2 warm-up and 3 timed lisa_td_loglike_batch calls with
+zero-noise data, autotunes the launch shapes (lisa_td_autotune), runs 2
+warm-up and 3 timed lisa_td_loglike_batch calls with
 the library's stage timing on, and reports logL evals/s, walker-samples/s and
 the share of the two largest stages.  Inputs are the seeded prior draws of
 workloads.prior_draws.
@@ -31,6 +32,7 @@ def point(W, days, precessing, orbit, precision, steps=3, warmup=2):
     p = torch.as_tensor(th, device="cuda")
     d = lk.tdi(lk.project(p[:1]))[:, :, 0].to(torch.float64).contiguous()
     lk.set_data(d)
+    api.lisa_td_autotune(lk.ctx, p, W)          # launch shapes for this point
     out = torch.empty(W, dtype=torch.float64, device="cuda")
     for _ in range(warmup):
         api.lisa_td_loglike_batch(lk.ctx, p, W, out)
