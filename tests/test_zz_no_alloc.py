@@ -70,3 +70,34 @@ def test_noalloc_matches_loglike_batch_on_two_calls(name, precision):
             assert close(got[w], want[w]), (call, w, got[w], want[w])
     lk.close()
     ref.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [3136, 20160, 21952])     # 2^6 7^2, 2^6 3^2 5 7, 2^6 7^3
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_norm_at_radix7_lengths_matches_oracle(n, precision):
+    """The DFT + PSD-weighted norm alone (Sec. II.B inner product) at lengths
+    whose FFT plans use radix-7 (and 5, 3) stages, against the oracle's
+    likelihood on the same residual.  The mixed path gets the oracle's
+    residual rounded to FP32, so only its FFT and norm arithmetic is compared:
+    a relative bar of 2e-5 on a sum of ~n/10 positive terms."""
+    from oracle import likelihood
+    from paper_2501_08261_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    W = 4
+    rng = np.random.default_rng(n + 10 * precision)
+    r = rng.normal(size=(3, n, W)) * 1e-21
+    if precision == 1:
+        r = r.astype(np.float32).astype(np.float64)
+    cfg = api.make_config(dt=5.0, n=n, precision=precision, tdi_gen=20)
+    rt = torch.as_tensor(r, dtype=torch.float64 if precision == 0 else torch.float32,
+                         device="cuda").contiguous()
+    got = torch.full((W,), float("nan"), dtype=torch.float64, device="cuda")
+    api.lisa_td_residual_loglike_noalloc(cfg, rt, W, got)
+    got = got.cpu().numpy()
+    zero = np.zeros((3, n))
+    for w in range(W):
+        want = likelihood.loglike(r[:, :, w], zero, 5.0, cfg.f_lo, cfg.f_hi, 20, 7)
+        bar = 1e-11 * abs(want) if precision == 0 else 2e-5 * abs(want)
+        assert abs(got[w] - want) <= bar, (n, precision, w, got[w], want)
