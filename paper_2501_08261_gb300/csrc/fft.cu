@@ -387,18 +387,33 @@ __global__ void __launch_bounds__(512) pass2_kernel(const typename CT<R>::T* __r
   }
 }
 
-__global__ void reduce_kernel(const double* __restrict__ partial, int nrp, int Wpad, int W,
-                              int mask, const WalkerRec* __restrict__ walkers, double* logl,
-                              int32_t* status) {
-  int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= W) return;
+// logL per walker from the per-row-pair partials: a block holds 32 walkers
+// (lanes, coalesced) x kRedWarps warps; warp q sums the (channel, row pair)
+// entries q, q + kRedWarps, ... of its lane's walker, then warp 0 adds the
+// warps' sums in order (deterministic).  One thread per walker walking all
+// 3 (n1/2 + 1) entries in series was bound by the latency of its L2 loads.
+constexpr int kRedWarps = 16;
+__global__ void __launch_bounds__(32 * kRedWarps) reduce_kernel(
+    const double* __restrict__ partial, int nrp, int Wpad, int W, int mask,
+    const WalkerRec* __restrict__ walkers, double* logl, int32_t* status) {
+  __shared__ double part[kRedWarps][32];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const int w = blockIdx.x * 32 + lane;
   double s = 0.0;
-  for (int c = 0; c < 3; ++c) {
-    if (!((mask >> c) & 1)) continue;
-    for (int r = 0; r < nrp; ++r) s += partial[((int64_t)c * nrp + r) * Wpad + w];
+  if (w < W) {
+    for (int c = 0; c < 3; ++c) {
+      if (!((mask >> c) & 1)) continue;
+      for (int r = q; r < nrp; r += kRedWarps) s += partial[((int64_t)c * nrp + r) * Wpad + w];
+    }
   }
-  int st = walkers[w].status;
-  logl[w] = st ? -INFINITY : -0.5 * s;
+  part[q][lane] = s;
+  __syncthreads();
+  if (q != 0 || w >= W) return;
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < kRedWarps; ++k) t += part[k][lane];
+  const int st = walkers[w].status;
+  logl[w] = st ? -INFINITY : -0.5 * t;
   if (status) status[w] = st;
 }
 
@@ -523,8 +538,9 @@ cudaError_t launch_fft_pass2(const lisa_td_ctx* c, int Wpad, cudaStream_t s) {
 
 cudaError_t launch_reduce(const lisa_td_ctx* c, int W, int Wpad, double* logl, int32_t* status,
                           cudaStream_t s) {
-  reduce_kernel<<<(W + 127) / 128, 128, 0, s>>>(c->partial, c->plan.n1 / 2 + 1, Wpad, W,
-                                                c->cfg.channel_mask, c->walkers, logl, status);
+  reduce_kernel<<<(W + 31) / 32, 32 * kRedWarps, 0, s>>>(c->partial, c->plan.n1 / 2 + 1, Wpad, W,
+                                                        c->cfg.channel_mask, c->walkers, logl,
+                                                        status);
   return cudaGetLastError();
 }
 
