@@ -43,13 +43,38 @@ __device__ inline void quat_euler(double a, double b, double g, double* q) {
   q[3] = cb * sin(0.5 * (a + g));
 }
 
+// n! and C(n, k): exact integers in double for n <= 20 and n <= 12.  Device
+// code reads them from constant-memory tables (the loop and the division
+// they replace give the same values, but cost FP64 multiplies and divides on
+// a pipe that runs at 1/64 of FP32); the host and larger arguments compute.
+static __constant__ double kFactTab[21] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0, 362880.0, 3628800.0, 39916800.0, 479001600.0, 6227020800.0, 87178291200.0, 1307674368000.0, 20922789888000.0, 355687428096000.0, 6402373705728000.0, 1.21645100408832e+17, 2.43290200817664e+18};
+static __constant__ double kBinomTab[13][13] = {
+    {1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 2.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 3.0, 3.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 4.0, 6.0, 4.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 5.0, 10.0, 10.0, 5.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 6.0, 15.0, 20.0, 15.0, 6.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 7.0, 21.0, 35.0, 35.0, 21.0, 7.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 8.0, 28.0, 56.0, 70.0, 56.0, 28.0, 8.0, 1.0, 0.0, 0.0, 0.0, 0.0},
+    {1.0, 9.0, 36.0, 84.0, 126.0, 126.0, 84.0, 36.0, 9.0, 1.0, 0.0, 0.0, 0.0},
+    {1.0, 10.0, 45.0, 120.0, 210.0, 252.0, 210.0, 120.0, 45.0, 10.0, 1.0, 0.0, 0.0},
+    {1.0, 11.0, 55.0, 165.0, 330.0, 462.0, 462.0, 330.0, 165.0, 55.0, 11.0, 1.0, 0.0},
+    {1.0, 12.0, 66.0, 220.0, 495.0, 792.0, 924.0, 792.0, 495.0, 220.0, 66.0, 12.0, 1.0}};
 __host__ __device__ inline double fact(int n) {
+#ifdef __CUDA_ARCH__
+  if (n >= 0 && n <= 20) return kFactTab[n];
+#endif
   double r = 1.0;
   for (int i = 2; i <= n; ++i) r *= i;
   return r;
 }
 __host__ __device__ inline double binom(int n, int k) {
   if (k < 0 || k > n) return 0.0;
+#ifdef __CUDA_ARCH__
+  if (n <= 12) return kBinomTab[n][k];
+#endif
   return fact(n) / (fact(k) * fact(n - k));
 }
 
