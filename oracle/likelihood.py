@@ -2,7 +2,7 @@
 log-likelihood (Sec. II.B, from "Once the three TDI channels ..." to the PSD
 equations).
 
-Readings (listed in DESIGN.md):
+Readings of the paper taken here:
 * logL = -1/2 sum_c (h_c - d_c | h_c - d_c) (the complete definition given in
   the footnote; the displayed form has the opposite sign of the cross term).
 * (a|b) = 4 df Re sum_{k: f_lo <= f_k <= f_hi} a_k conj(b_k) / S(f_k),

@@ -1,7 +1,7 @@
 """Time-domain LISA response (Sec. II.B): link responses y_slr (Eq. yslr),
 TDI Michelson X 1.5 / 2.0, Y and Z by cyclic permutation, and A, E, T.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here:
 * h at the off-grid times t_s, t_r and y at the delayed TDI times come from
   centred Lagrange interpolation of order p (odd; p = 1 is the paper's linear
   interpolation, Sec. II.B end); samples outside the grid are zero.
