@@ -1,7 +1,7 @@
 /*
  * lisa_sampler.h -- C ABI of the sampler's proposal and accept steps for the
- * batched likelihood of lisa_td.h (arXiv:2501.08261, Sec. II.C "Fisher
- * initialization": starting points drawn from a Gaussian with mean at the
+ * batched likelihood of lisa_td.h (arXiv:2501.08261, Sec. II.C, Fisher
+ * initialization: starting points drawn from a Gaussian with mean at the
  * injection and covariance equal to the inverse Fisher matrix, the Fisher
  * matrix built from finite differences of the likelihood; the sampler accepts
  * or rejects every proposal by the exact likelihood).

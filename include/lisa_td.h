@@ -72,8 +72,8 @@ typedef struct {
 
 /* Create a context: validates cfg, builds the orbit tables (one kernel, FP64),
  * the PSD weights of the band bins and the FFT plan, and allocates the
- * workspace for cfg->max_walkers walkers.  Sec. II.B: orbits "only need to be
- * computed once".  On error *out is set to NULL. */
+ * workspace for cfg->max_walkers walkers.  Sec. II.B: the orbit quantities
+ * are computed once, not per likelihood call.  On error *out is set to NULL. */
 int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream);
 
 /* Store the data d (A, E, T time series; FP64 device [3][n], row c = A,E,T).

@@ -26,7 +26,7 @@ KEPLER_E0 = ARM_SI / (2.0 * math.sqrt(3.0) * AU_SI)
 KEPLER_ETA = (0.0, 0.01, -0.01)
 
 # --- Sangria analytic noise (Sec. II.B, PSD equations) -----------------
-A_ACC = 2.4e-15                          # acceleration noise amplitude (reading, see DESIGN)
+A_ACC = 2.4e-15                          # acceleration noise amplitude (a reading: the printed value is garbled)
 A_OMS = 7.9e-12                          # optical metrology amplitude
 
 # --- waveform stand-in (declared) --------------------------------------

@@ -1,6 +1,6 @@
 """Fourier transform, Sangria analytic PSD, matched-filter inner product and
-log-likelihood (Sec. II.B, from "Once the three TDI channels ..." to the PSD
-equations).
+log-likelihood (Sec. II.B: the inner product of the A, E, T channels and the
+PSD equations).
 
 Readings of the paper taken here:
 * logL = -1/2 sum_c (h_c - d_c | h_c - d_c) (the complete definition given in

@@ -1,6 +1,5 @@
-"""Spacecraft orbits and link light times (Sec. II.B: "the positions of the
-sender and receiver and the light travel time in each link must be tracked
-over the whole observation period").
+"""Spacecraft orbits and link light times (Sec. II.B: the response needs both
+ends' positions and every link's light time at each time of the observation).
 
 Positions are in light-seconds in an ecliptic SSB frame.  Two declared models:
 
@@ -12,7 +11,7 @@ Positions are in light-seconds in an ecliptic SSB frame.  Two declared models:
   i_k = sqrt(3) e_k, node turned by 2 pi (k-1)/3).  Light times solve
   |r_r(t) - r_s(t - L)| = L (light-seconds) by fixed-point iteration.
 
-Link convention (Sec. II.B, "y_slr ... convention in Fig. 1 of radler"):
+Link convention (Sec. II.B; y_slr labelled as in the TDI reference it cites):
 link l is the arm opposite spacecraft |l|; +l and -l are its two directions.
 """
 import math

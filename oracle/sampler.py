@@ -1,5 +1,5 @@
 """Fisher-Gaussian proposal and exact-likelihood Metropolis-Hastings step
-(Sec. II.C, "Fisher initialization"; the sampler's accept rule).
+(Sec. II.C, Fisher initialization; the sampler's accept rule).
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 

@@ -1,4 +1,5 @@
-// Create-time tables (Sec. II.B: orbits "only need to be computed once"):
+// Create-time tables (Sec. II.B: the orbit quantities are computed once, not
+// per likelihood call):
 // spacecraft positions, emission positions and light times per grid sample,
 // the PSD weights of the band bins, FFT twiddles, and the data copy.
 #include <math.h>
