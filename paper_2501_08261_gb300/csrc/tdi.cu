@@ -123,6 +123,30 @@ __device__ inline double term_delay_at(const TdiTerm& T, const int8_t* __restric
   return D;
 }
 
+// one delayed term of one lane with its own weights (lanes of a warp whose
+// window starts differ, in ragged batches); kept out of line so that its
+// weight array does not crowd the registers of the shared-weight path
+template <int K>
+__device__ __noinline__ double fp64_lane_term(double eps, int64_t loc, int64_t base, int64_t lo,
+                                              int rows, const double* __restrict__ ywin,
+                                              const double* __restrict__ cinv,
+                                              const double* __restrict__ y, int64_t row0,
+                                              int64_t n, int ldw_in, int w, int W, int lane) {
+  double wts[K];
+  lagrange_weights<double, K>(eps, cinv, wts);
+  double v = 0.0;
+  if (loc >= 0 && loc + K <= rows) {
+#pragma unroll
+    for (int m = 0; m < K; ++m) v += wts[m] * ywin[(loc + m) * kPW + lane];
+  } else {
+    for (int m = 0; m < K; ++m) {
+      const int64_t g = base + m;
+      if (g >= lo && g >= 0 && g < n && w < W) v += wts[m] * y[(row0 + g) * ldw_in + w];
+    }
+  }
+  return v;
+}
+
 template <int K, int SPT>
 __global__ void __launch_bounds__(128) tdi_fp64_kernel(
     const TdiTable* __restrict__ tab, int W, int ldw_in, int ldw_out, int64_t n, double dt,
@@ -139,14 +163,17 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
   const int rows = TILE + hl + hr;
   if (woff && group_inactive(woff + blockIdx.y * 32, 32, i0 + TILE)) return;
   const int64_t lo = woff ? woff[w] : 0;        // rows before lo: outside the walker's window
+  // the delays depend on the sample only, so with a common window start all
+  // lanes of a warp need the same Lagrange weights: lane m then evaluates
+  // weight m alone and the taps take it by shuffle (a third of the FP64
+  // instructions of every lane evaluating all K, on GB300's 1/64-rate pipe)
+  const bool shared_w = !woff || __all_sync(0xffffffffu, lo == __shfl_sync(0xffffffffu, lo, 0));
+  constexpr int H = (K - 2) / 2;
   if (warp == 0 && lane < K) cinv_s[lane] = lagrange_denom_inv<double, K>(lane);
   double ax[SPT], ay[SPT], az[SPT];      // X, Y, Z accumulators
 #pragma unroll
   for (int s = 0; s < SPT; ++s) ax[s] = ay[s] = az[s] = 0.0;
   __syncthreads();
-  double cinv[K];
-#pragma unroll
-  for (int j = 0; j < K; ++j) cinv[j] = cinv_s[j];
 
   for (int j = 0; j < kNLink; ++j) {
     __syncthreads();
@@ -172,19 +199,31 @@ __global__ void __launch_bounds__(128) tdi_fp64_kernel(
           const double D = term_delay_at(T, tab->chain[j][q], orb, n, i, dt, nested);
           double tau = (double)(i - lo) - D / dt;    // relative to the window start
           double fl = floor(tau);
-          double wts[K];
-          lagrange_weights<double, K>(tau - fl, cinv, wts);
+          const double eps = tau - fl;
           int64_t base = lo + (int64_t)fl - (K - 2) / 2;
           int64_t loc = base - (i0 - hl);
           v = 0.0;
-          if (loc >= 0 && loc + K <= rows) {
+          if (shared_w) {
+            double wm = 0.0;                         // this lane's weight (lanes < K)
+            if (lane < K) {
+              wm = cinv_s[lane];
 #pragma unroll
-            for (int m = 0; m < K; ++m) v += wts[m] * ywin[(loc + m) * kPW + lane];
-          } else {
-            for (int m = 0; m < K; ++m) {
-              int64_t g = base + m;
-              if (g >= lo && g >= 0 && g < n && w < W) v += wts[m] * y[((int64_t)j * n + g) * ldw_in + w];
+              for (int m = 0; m < K; ++m) wm *= m == lane ? 1.0 : eps - (double)(m - H);
             }
+            if (loc >= 0 && loc + K <= rows) {       // warp-uniform: loc is common
+#pragma unroll
+              for (int m = 0; m < K; ++m)
+                v += __shfl_sync(0xffffffffu, wm, m) * ywin[(loc + m) * kPW + lane];
+            } else {
+              for (int m = 0; m < K; ++m) {
+                const double wk = __shfl_sync(0xffffffffu, wm, m);
+                int64_t g = base + m;
+                if (g >= lo && g >= 0 && g < n && w < W) v += wk * y[((int64_t)j * n + g) * ldw_in + w];
+              }
+            }
+          } else {
+            v = fp64_lane_term<K>(eps, loc, base, lo, rows, ywin, cinv_s, y, (int64_t)j * n, n,
+                                  ldw_in, w, W, lane);
           }
         }
         v *= (double)T.sign;
