@@ -2,6 +2,17 @@
 twist-up of its precessing members (Sec. II.A, the three displayed equations
 h^J = sum D* h^CP, h^L0 = sum D* h^J, h+ - i hx = sum h^L0 -2Y).
 
+Reading of the twist-up (the paper does not fix its Wigner-D phase
+convention): the paper's D^l_{m m'}(alpha, beta, gamma) is taken as
+e^{+i m alpha} d^l_{m m'}(beta) e^{+i m' gamma}, the complex conjugate of the
+textbook ``wigner.wigner_D``.  With it the printed sums of D* rotate the
+co-precessing frame by R(alpha, beta, gamma) = Rz(alpha) Ry(beta) Rz(gamma):
+the CP axes are R applied to the J axes, so L sits at polar angle beta and
+azimuth alpha in the J frame.  The J -> L0 step is the rotation R(rot0).
+Pinned against 3-vector geometry (rotating the line of sight and its
+polarisation basis, no Wigner matrix) by
+``test_twist_up_is_the_rotation_of_the_emission_pattern``.
+
 The paper uses IMRPhenomT(HM)(P)(HM) but takes its coefficients from earlier
 work; the stand-in keeps the same structure -- every time sample is an
 independent closed form, modes (2,+-2),(2,+-1),(3,+-3),(3,+-2),(4,+-4),
@@ -197,6 +208,12 @@ def euler_angles(src, t):
     return alpha, beta, gamma, rot0
 
 
+def paper_D(l, m, mp, alpha, beta, gamma):
+    """The Wigner-D of the twist-up equations (Sec. II.A) under the reading in
+    the module docstring: e^{+i m alpha} d^l_{m mp}(beta) e^{+i mp gamma}."""
+    return np.conj(wigner_D(l, m, mp, alpha, beta, gamma))
+
+
 def plus_cross(theta, t, t0, mode_mask, precessing):
     """h+ and hx in the (u, v) frame after the polarisation rotation by psi:
     (h+ - i hx) -> (h+ - i hx) exp(2 i psi)  (Sec. III.A)."""
@@ -224,12 +241,12 @@ def plus_cross(theta, t, t0, mode_mask, precessing):
             for mm in range(-l, l + 1):                 # first rotation, CP -> J
                 acc = np.zeros(t.shape, dtype=np.complex128)
                 for mp, h in cp.items():
-                    acc += np.conj(wigner_D(l, mm, mp, alpha, beta, gamma)) * h
+                    acc += np.conj(paper_D(l, mm, mp, alpha, beta, gamma)) * h
                 hJ[mm] = acc
             for mm in range(-l, l + 1):                 # second rotation, J -> L0
                 acc = np.zeros(t.shape, dtype=np.complex128)
                 for mp in range(-l, l + 1):
-                    acc += np.conj(wigner_D(l, mm, mp, *rot0)) * hJ[mp]
+                    acc += np.conj(paper_D(l, mm, mp, *rot0)) * hJ[mp]
                 hpc += acc * sYlm(-2, l, mm, iota, phr)
     hpc = hpc * np.exp(2j * src["psi"])
     return hpc.real, -hpc.imag

@@ -121,10 +121,11 @@ __global__ void prep_kernel(const double* __restrict__ params, int W, int Wpad, 
   R.G_ref = prec_G(aref, b, Sc);
   R.gamma_ref = kPi - ph1;
   double beta_ref = atan2(b, aref);
-  // inverse of q(-alpha0, beta0, -gamma0) with (alpha0, beta0, gamma0) =
-  // (phi1 - pi, -beta_ref, 0), composed with q(phi_ref, iota, 0)
+  // inverse of q(alpha0, beta0, gamma0), the J -> L0 rotation with
+  // (alpha0, beta0, gamma0) = (phi1 - pi, -beta_ref, 0), composed with
+  // q(phi_ref, iota, 0)
   double q0[4], q0i[4];
-  quat_euler(-(ph1 - kPi), -beta_ref, 0.0, q0);
+  quat_euler(ph1 - kPi, -beta_ref, 0.0, q0);
   q0i[0] = q0[0]; q0i[1] = -q0[1]; q0i[2] = -q0[2]; q0i[3] = -q0[3];
   qmul(q0i, qy, R.q03);
   R.status = ok ? 0 : 1;

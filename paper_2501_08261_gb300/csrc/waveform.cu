@@ -37,7 +37,7 @@ __device__ void polar_fp64(const WalkerRec& W, double t, int precessing, double&
     double sp, cp, sm, cm;
     sincos(0.5 * (al + ga), &sp, &cp);
     sincos(0.5 * (al - ga), &sm, &cm);
-    double q1[4] = {cbh * cp, -sbh * sm, -sbh * cm, cbh * sp};   // q(-al, be, -ga)^-1
+    double q1[4] = {cbh * cp, sbh * sm, -sbh * cm, -cbh * sp};   // q(al, be, ga)^-1
     qmul(q1, W.q03, qT);
   }
   for (int j = 0; j < W.nmode; ++j) {
@@ -231,7 +231,7 @@ __device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessi
     float hm = df_mod_2pi({0.5f * sm2.hi, 0.5f * sm2.lo});
     sincosf(hp, &sp, &cp);
     sincosf(hm, &sm, &cm);
-    float q1[4] = {cbh * cp, -sbh * sm, -sbh * cm, cbh * sp};
+    float q1[4] = {cbh * cp, sbh * sm, -sbh * cm, -cbh * sp};   // q(al, be, ga)^-1
     const float* b = X.q03;
     qT[0] = q1[0] * b[0] - q1[1] * b[1] - q1[2] * b[2] - q1[3] * b[3];
     qT[1] = q1[0] * b[1] + q1[1] * b[0] + q1[2] * b[3] - q1[3] * b[2];

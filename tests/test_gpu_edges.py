@@ -89,3 +89,61 @@ def test_mixed_path_at_each_lagrange_order(p):
         o = pipeline.loglike(th[w], s, d)
         assert abs(got[w] - o) <= max(0.05, 1e-4 * abs(o)), (p, w, got[w], o)
     lk.close()
+
+
+def _edge_walkers(base, precessing, n, dt):
+    """The method's degenerate cases around one source: the bodies given in
+    the wrong order (m2 > m1, the swap rule), the merger before the grid
+    starts and after it ends, face-on and face-off inclinations, and for
+    precessing spins no spin on body 1 and tilts of 0 and pi (beta -> 0, pi,
+    the limits of the quaternion Wigner-D)."""
+    out, names = [base.copy()], ["base"]
+
+    def add(name, **kv):
+        w = base.copy()
+        for k, v in kv.items():
+            w[int(k[1:])] = v
+        out.append(w)
+        names.append(name)
+    add("m2>m1", p0=base[1], p1=base[0], p2=base[5], p3=base[6], p4=base[7],
+        p5=base[2], p6=base[3], p7=base[4])
+    add("merger_before_t0", p14=-600.0)
+    add("merger_after_end", p14=n * dt + 3.0 * 3600.0)
+    add("iota=0", p9=0.0)
+    add("iota=pi", p9=np.pi)
+    if precessing:
+        add("a1=0", p2=0.0)
+        add("tilt1=0", p3=0.0)
+        add("tilt1=pi", p3=np.pi)
+        add("both_tilts_pi", p3=np.pi, p6=np.pi)
+    return np.array(out), names
+
+
+@pytest.mark.parametrize("name", ["c2_hm_1d", "c3_prec_1d"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_degenerate_cases_match_oracle(name, precision):
+    cfg = workloads.config(name)
+    prec = bool(cfg["precessing"])
+    s = oracle_setup(cfg)
+    base = workloads.prior_draws(1, cfg["n"], cfg["dt"], 91, precessing=prec,
+                                 logm=(5.8, 6.3))[0]
+    th, names = _edge_walkers(base, prec, cfg["n"], cfg["dt"])
+    d = pipeline.aet(base, s)
+    far = base.copy()
+    far[8] = 1e30
+    rho = np.sqrt(-2.0 * pipeline.loglike(far, s, d))
+    d = d * (500.0 / rho)
+    th[:, 8] *= rho / 500.0
+    W = th.shape[0]
+    lk = api.Likelihood(precision=precision, max_walkers=W, **gpu_kwargs(cfg))
+    lk.set_data(_t(d))
+    got, st = lk.loglike(_t(th), with_status=True)
+    got, st = got.cpu().numpy(), st.cpu().numpy()
+    assert np.all(st == 0), dict(zip(names, st))
+    for w in range(W):
+        o = pipeline.loglike(th[w], s, d)
+        tol = max(1e-6, 1e-11 * abs(o)) if precision == 0 else max(0.05, 1e-4 * abs(o))
+        assert abs(got[w] - o) <= tol, (names[w], got[w], o)
+    # the swap rule: the same binary with its bodies listed the other way round
+    assert abs(got[1] - got[0]) <= (1e-9 if precision == 0 else 1e-3) * max(1.0, abs(got[0]))
+    lk.close()

@@ -6,14 +6,20 @@ each restated here in Python and compared with an independent reference:
 * the projection's paired Lagrange weights: nodes o and 1 - o paired as
   s + o (1 - o) with s = eps (eps - 1), the 1 / prod (j - m) absorbed into
   per-pair scalings, give the centred Lagrange weights (oracle);
-* the radix-5 and radix-7 butterflies in symmetric form give the DFT.
+* the radix-5 and radix-7 butterflies in symmetric form give the DFT;
+* the waveform kernels' single-sum twist-up (Eq. newtwistup): the unit
+  quaternion of each Euler rotation, their Hamilton product
+  conj(q(alpha, beta, gamma)) conj(q(rot0)) q(phi_ref, iota, 0), and
+  sqrt((2l+1)/4pi) D^l_{m,2} as a sum of non-negative powers of
+  Q_a = q0 + i q3, Q_b = q2 + i q1, equal the oracle's two-step twist-up.
 """
 import math
 
 import numpy as np
 import pytest
 
-from oracle import response
+from oracle import consts as K
+from oracle import response, waveform
 
 
 def _div_magic(j, L):
@@ -82,3 +88,99 @@ def test_symmetric_odd_radix_butterflies_are_the_dft(R):
     for _ in range(20):
         a = rng.normal(size=R) + 1j * rng.normal(size=R)
         assert np.max(np.abs(_dft_sym(a, R) - np.fft.fft(a))) <= 1e-13
+
+
+def _quat_euler(a, b, g):
+    cb, sb = math.cos(0.5 * b), math.sin(0.5 * b)
+    return np.array([cb * math.cos(0.5 * (a + g)), -sb * math.sin(0.5 * (a - g)),
+                     sb * math.cos(0.5 * (a - g)), cb * math.sin(0.5 * (a + g))])
+
+
+def _qmul(a, b):
+    return np.array([a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3],
+                     a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2],
+                     a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1],
+                     a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0]])
+
+
+def _conj(q):
+    return np.array([q[0], -q[1], -q[2], -q[3]])
+
+
+def _ylm_from_quat(l, m, q):
+    Qa, Qb = complex(q[0], q[3]), complex(q[2], q[1])
+    acc = 0j
+    for r in range(max(0, m - 2), min(l + m, l - 2) + 1):
+        c = math.comb(l + m, r) * math.comb(l - m, l - 2 - r) * (-1.0) ** r
+        acc += c * Qa ** (l + m - r) * Qa.conjugate() ** (l - 2 - r) * \
+            Qb ** (2 - m + r) * Qb.conjugate() ** r
+    f = math.factorial
+    return acc * math.sqrt(f(l + 2) * f(l - 2) / (f(l + m) * f(l - m))) * \
+        math.sqrt((2 * l + 1) / (4 * math.pi))
+
+
+@pytest.mark.parametrize("tilt", [0.3, 1.6, 2.9])
+def test_quaternion_single_sum_equals_the_oracle_twist_up(tilt):
+    th = np.array([6.2e5, 1.9e5, 0.8, tilt, 1.1, 0.4, 0.9, 2.0, 5.0, 0.7, 2.3,
+                   0.2, 4.0, 0.0, 0.9 * 10 * 86400.0])
+    src = waveform.source(th, True)
+    t = np.linspace(src["tm"] - 3e5, src["tm"] + 300.0, 24)
+    al, be, ga, rot0 = waveform.euler_angles(src, t)
+    hp, hx = waveform.plus_cross(th, t, 0.0, 31, True)
+    want = hp - 1j * hx
+    q03 = _qmul(_conj(_quat_euler(*rot0)), _quat_euler(src["phi_ref"], src["iota"], 0.0))
+    got = np.zeros(t.size, complex)
+    for (l, m) in K.MODES:
+        h = waveform.mode(src, l, m, t, 0.0)
+        for i in range(t.size):
+            qT = _qmul(_conj(_quat_euler(al[i], be[i], ga[i])), q03)
+            got[i] += h[i] * _ylm_from_quat(l, m, qT) + \
+                (-1.0) ** l * np.conj(h[i]) * _ylm_from_quat(l, -m, qT)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+def _difference_weights(eps, K):
+    """C_m (m = -H .. H) of the summation-by-parts form used by the mixed TDI
+    tile tables: y(c + eps) = y_c + sum_m C_m (y_{c+m+1} - y_{c+m})."""
+    H = (K - 2) // 2
+    w = response.lagrange_weights(eps, K - 1)
+    C = np.zeros(K - 1)
+    for mi in range(K - 1):
+        m = mi - H
+        for k in range(K):
+            o = k - H
+            if m >= 0 and o > m:
+                C[mi] += w[k]
+            if m < 0 and o <= m:
+                C[mi] -= w[k]
+    return C
+
+
+def test_combined_pair_fir_equals_the_sum_of_its_terms():
+    """The mixed TDI kernel's per-(channel, link) FIR: the difference weights of
+    the pair's terms added at offsets bo - H - min(bo - H) into G, applied to dy
+    from row s + min(bo - H), plus each term's centre sample, give the signed
+    sum of the terms' Lagrange interpolations."""
+    K, H = 32, 15
+    rng = np.random.default_rng(4)
+    t = np.arange(400)
+    y = np.sin(0.05 * t) + 0.3 * np.cos(0.013 * t + 1.0) + 0.01 * rng.normal(size=t.size)
+    dy = np.append(np.diff(y), 0.0)
+    bos = [-2, -5, -9, -12]
+    sgs = [1.0, -1.0, 1.0, -1.0]
+    epss = rng.uniform(0.0, 1.0, 4)
+    bmin = min(b - H for b in bos)
+    ntap = max(b - H for b in bos) - bmin + K - 1
+    G = np.zeros(ntap)
+    for b, sg, e in zip(bos, sgs, epss):
+        o = b - H - bmin
+        G[o:o + K - 1] += sg * _difference_weights(e, K)
+    for s in range(150, 250, 7):
+        got = sum(sg * y[s + b] for b, sg in zip(bos, sgs))
+        got += float(np.dot(G, dy[s + bmin:s + bmin + ntap]))
+        want = 0.0
+        for b, sg, e in zip(bos, sgs, epss):
+            w = response.lagrange_weights(e, K - 1)
+            c = s + b
+            want += sg * float(np.dot(w, y[c - H:c - H + K]))
+        assert abs(got - want) <= 1e-12, (s, got, want)

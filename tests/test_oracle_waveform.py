@@ -232,16 +232,20 @@ def test_precessing_without_spin_equals_aligned():
 
 
 def test_two_step_equals_single_rotation_sum():
-    """The two sums of D* collapse to one D* of the composed rotation
-    (the identity behind the single-sum form, Eq. newtwistup)."""
+    """The two sums of the twist-up collapse to one sum over the composed
+    rotation (the identity behind the single-sum form, Eq. newtwistup)."""
     src = waveform.source(THETA_PR, True)
     t = np.array([src["tm"] - 5e4])
     al, be, ga, rot0 = waveform.euler_angles(src, t)
     Rt = _rot(*rot0) @ _rot(al[0], be[0], ga[0])
     a, b, g = _euler(Rt)
+
+    def Dp(l, *ang):
+        ms = range(-l, l + 1)
+        return np.array([[waveform.paper_D(l, m, mp, *ang) for mp in ms] for m in ms])
     for l in (2, 3, 4):
-        two = _Dmat(l, *rot0).conj() @ _Dmat(l, al[0], be[0], ga[0]).conj()
-        assert np.allclose(two, _Dmat(l, a, b, g).conj(), atol=1e-12)
+        two = Dp(l, *rot0).conj() @ Dp(l, al[0], be[0], ga[0]).conj()
+        assert np.allclose(two, Dp(l, a, b, g).conj(), atol=1e-12)
 
 
 def test_reference_frame_at_reference_time_is_identity():
@@ -264,3 +268,86 @@ def test_table1_injection_runs_and_is_finite():
     hp, hc = waveform.plus_cross(th, t, 0.0, 31, True)
     assert np.all(np.isfinite(hp)) and np.max(np.abs(hp)) > 0
     assert g["dt_s"] == 10.0 and g["snr_approx"] == 2800
+
+
+# ------------------------------------- twist-up against 3-vector geometry ----
+def _spherical_basis(n):
+    """Polar angles of the unit vector n and the tangent vectors e_theta, e_phi there."""
+    th = math.acos(max(-1.0, min(1.0, n[2])))
+    ph = math.atan2(n[1], n[0])
+    e_th = np.array([math.cos(th) * math.cos(ph), math.cos(th) * math.sin(ph), -math.sin(th)])
+    e_ph = np.array([-math.sin(ph), math.cos(ph), 0.0])
+    return th, ph, e_th, e_ph
+
+
+def _strain_seen_through_rotation(cp_modes, M, iota, phi):
+    """h+, hx along the direction (iota, phi) of the L0 frame when the source's
+    co-precessing frame has axes M e_x, M e_y, M e_z in L0 coordinates.
+
+    No Wigner matrix enters: the line of sight and its polarisation basis are
+    carried into the co-precessing frame by the 3x3 matrix M^T, the strain is
+    the mode sum h+ - i hx = sum h_lm -2Y_lm there, rebuilt as the transverse
+    tensor h+(e_th e_th - e_ph e_ph) + hx(e_th e_ph + e_ph e_th), and projected
+    back onto the carried basis."""
+    n0 = np.array([math.sin(iota) * math.cos(phi), math.sin(iota) * math.sin(phi), math.cos(iota)])
+    _, _, a0, b0 = _spherical_basis(n0)
+    n, a, b = M.T @ n0, M.T @ a0, M.T @ b0
+    th, ph, e_th, e_ph = _spherical_basis(n)
+    H = sum(h * sYlm(-2, l, m, th, ph) for (l, m), h in cp_modes.items())
+    hp, hx = H.real, -H.imag
+    T = (hp[:, None, None] * (np.outer(e_th, e_th) - np.outer(e_ph, e_ph))
+         + hx[:, None, None] * (np.outer(e_th, e_ph) + np.outer(e_ph, e_th)))
+    plus = 0.5 * (np.einsum("i,tij,j->t", a, T, a) - np.einsum("i,tij,j->t", b, T, b))
+    cross = np.einsum("i,tij,j->t", a, T, b)
+    return plus, cross
+
+
+@pytest.mark.parametrize("angles,rot0", [
+    ((0.7, 0.3, -1.1), (0.0, 0.0, 0.0)),
+    ((-2.0, math.pi / 2, 0.4), (0.0, 0.0, 0.0)),
+    ((1.3, math.pi - 0.2, 2.2), (0.0, 0.0, 0.0)),
+    ((0.9, 0.0, -0.35), (0.0, 0.0, 0.0)),            # pure z-rotation
+    ((0.7, 0.3, -1.1), (2.5, -0.45, 0.0)),           # both rotations generic
+    ((-0.6, 1.9, 0.8), (-1.2, -1.3, 0.6)),
+])
+def test_twist_up_is_the_rotation_of_the_emission_pattern(monkeypatch, angles, rot0):
+    """The two-step twist-up of ``plus_cross`` (Sec. II.A, the two sums of D*
+    and the sum with -2Y) must equal what plain 3-vector geometry gives for a
+    co-precessing frame whose axes are R(alpha,beta,gamma) = Rz(alpha)Ry(beta)Rz(gamma)
+    applied to the J axes (so L points at polar angle beta, azimuth alpha in
+    the J frame), and a J -> L0 map R(rot0).  The Euler angles are frozen to
+    constants so the identity holds sample by sample; a Wigner D in place of
+    D*, swapped indices or the inverse rotation each break it."""
+    th = np.array(THETA_PR, dtype=float)
+    th[13] = 0.0                                     # no polarisation rotation
+    src = waveform.source(th, True)
+    t = np.linspace(src["tm"] - 4e4, src["tm"] + 200.0, 64)
+
+    def frozen(src_, t_):
+        one = np.ones(np.shape(t_))
+        return angles[0] * one, angles[1] * one, angles[2] * one, rot0
+    monkeypatch.setattr(waveform, "euler_angles", frozen)
+    hp, hx = waveform.plus_cross(th, t, 0.0, 31, True)
+
+    cp = {}
+    for (l, m) in K.MODES:
+        h = waveform.mode(src, l, m, t, 0.0)
+        cp[(l, m)] = h
+        cp[(l, -m)] = (-1.0) ** l * np.conj(h)
+    M = _rot(*rot0) @ _rot(*angles)
+    gp, gx = _strain_seen_through_rotation(cp, M, src["iota"], src["phi_ref"])
+    scale = max(np.max(np.abs(gp)), np.max(np.abs(gx)))
+    assert scale > 0
+    assert np.max(np.abs(hp - gp)) < 1e-12 * scale
+    assert np.max(np.abs(hx - gx)) < 1e-12 * scale
+
+
+def test_geometric_strain_reduces_to_mode_sum_without_rotation():
+    """With M = identity the geometric construction is the plain mode sum."""
+    rng = np.random.default_rng(7)
+    cp = {(l, m): rng.normal(size=5) + 1j * rng.normal(size=5)
+          for l in (2, 3) for m in range(-l, l + 1)}
+    iota, phi = 1.1, -0.4
+    gp, gx = _strain_seen_through_rotation(cp, np.eye(3), iota, phi)
+    H = sum(h * sYlm(-2, l, m, iota, phi) for (l, m), h in cp.items())
+    assert np.allclose(gp, H.real, atol=1e-14) and np.allclose(gx, -H.imag, atol=1e-14)
