@@ -34,8 +34,7 @@ FLOPS_PROJECT = 9 * (2 * 2 * K_TAPS + 4 * K_TAPS) + 6 * 32 + 9 * 5        # 2541
 FLOPS_TDI2 = 42 * 2 * K_TAPS + 6 + 10                                     # 2704
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5, max clock
 # DRAM bytes (read + write) per walker-sample of each kernel, from one ncu
-# capture of 30 d x 64 walkers (profiles/tdi_mixed_kernel_30d_64w.md,
-# profiles/project_mixed_kernel_30d_64w.md); traffic scales with walker-samples.
+# capture of 30 d x 64 walkers; traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
 NCU_BYTES_PER_UNIT = {"tdi": 1228.392704e6 / (518400 * 64),
                       "project": 1216.544000e6 / (518400 * 64)}

@@ -186,9 +186,12 @@ int lisa_td_profile_read(lisa_td_ctx* ctx, double* stage_ms, int64_t* calls);
  * Limit: all scratch lives in one static 32 MiB device array, held on every
  * GPU that loads the library until the process exits; about 3 n W x 8 (FP64)
  * or x 4 (mixed) bytes are needed, and larger (n, W) fail with LISA_TD_ERANGE
- * (n = 17280 allows W <= 78 in FP64, W <= 158 mixed).  The first call on each device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the array: calls that can
+ * (n = 17280 allows W <= 78 in FP64, W <= 156 mixed).  dt must be finite and
+ * > 0.  Each call made outside stream capture looks up the array's device
+ * address (cudaGetSymbolAddress) and keeps it; a call on a capturing stream
+ * uses the address kept by the last uncaptured call on that device, so make
+ * one call before any stream capture, and one more after a cudaDeviceReset
+ * before capturing again.  Every call shares the array: calls that can
  * overlap on the GPU (different streams, or several host threads) race and
  * give wrong results; order them on one stream. */
 int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_dev, int32_t W,

@@ -43,7 +43,8 @@ __global__ void noalloc_setup_kernel(int mask, int* chans, int* walker_words, in
 
 int check(const lisa_td_config* g, const void* r, int32_t W, const double* out) {
   if (!g || !r || !out) return report_error(LISA_TD_EINVAL, "noalloc: NULL argument");
-  if (!(g->dt > 0.0)) return report_error(LISA_TD_EINVAL, "noalloc: dt must be > 0");
+  if (!(g->dt > 0.0) || !isfinite(g->dt))
+    return report_error(LISA_TD_EINVAL, "noalloc: dt must be finite and > 0");
   if (g->n < 64 || g->n > (int64_t(1) << 24)) return report_error(LISA_TD_ERANGE, "noalloc: n out of [64, 2^24]");
   if (!(g->f_lo >= 0.0) || !(g->f_hi > g->f_lo))
     return report_error(LISA_TD_EINVAL, "noalloc: band must satisfy 0 <= f_lo < f_hi");
@@ -99,15 +100,26 @@ extern "C" int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return report_error(LISA_TD_ECUDA, "noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return report_error(LISA_TD_ERANGE, "noalloc: device %d above %d", dev, kMaxDevices);
+  // Outside stream capture the address is looked up on every call, so a
+  // device reset (after which the module and its array are loaded again) never
+  // leaves a stale pointer; during capture the address of the last call made
+  // outside capture is used.
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cap);
+  if (e != cudaSuccess) return report_error(LISA_TD_ECUDA, "noalloc: cudaStreamIsCapturing: %s", cudaGetErrorString(e));
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess)
         return report_error(LISA_TD_ECUDA, "noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
       g_scratch_addr[dev] = p;
+    } else if (!g_scratch_addr[dev]) {
+      return report_error(LISA_TD_EINVAL,
+                          "noalloc: the first call on a device must come before stream capture");
     }
     base = (unsigned char*)g_scratch_addr[dev];
   }
@@ -119,7 +131,6 @@ extern "C" int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const
   c.walkers = (WalkerRec*)(base + off[5]);
   c.fy = base + off[6];
   c.partial = (double*)(base + off[7]);
-  cudaStream_t s = (cudaStream_t)stream;
   const int64_t nwords = (int64_t)(sizeof(WalkerRec) * (size_t)W / sizeof(int));
   noalloc_setup_kernel<<<(unsigned)((nwords + 255) / 256 > 0 ? (nwords + 255) / 256 : 1), 256, 0, s>>>(
       cfg->channel_mask, c.chan_list, (int*)c.walkers, nwords);

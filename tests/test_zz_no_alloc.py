@@ -28,6 +28,18 @@ def test_rejects_sizes_beyond_the_static_scratch():
     assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), fake, 3, fake, None) == -1
     assert b"even" in lib.lisa_td_last_error()
     assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), None, 2, fake, None) == -1
+    inf_dt = api.make_config(dt=float("inf"), n=17280, precision=1)
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(inf_dt), fake, 2, fake, None) == -1
+    assert b"dt" in lib.lisa_td_last_error()
+    # the mixed path's boundary at n = 17280: W = 158 needs more than the array
+    mixed = api.make_config(dt=5.0, n=17280, precision=1)
+    assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(mixed), fake, 158, fake, None) == -5
+    if not torch.cuda.is_available():
+        # W = 156 (and W = 78 in FP64) pass every size check and stop only at the
+        # first CUDA call, which fails on a machine without a GPU; on a GPU
+        # machine the fake pointers would be used, so this part runs only here
+        assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(mixed), fake, 156, fake, None) == -3
+        assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), fake, 78, fake, None) == -3
 
 
 def _walkers(cfg, w, seed):
