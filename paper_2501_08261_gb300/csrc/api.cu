@@ -43,7 +43,8 @@ void free_ctx(lisa_td_ctx* c) {
   }
   void* ptrs[] = {c->orb64, c->orb32, c->psdw, c->plan.tw_n, c->plan.tw1, c->plan.tw2,
                   c->tdi_tab, c->chan_list, c->data64, c->data32, c->walkers, c->h, c->y,
-                  c->r, c->fy, c->partial, c->status, c->tdi_tiles};
+                  c->r, c->fy, c->partial, c->status, c->tdi_tiles, c->tdi_pairs,
+                  c->tdi_flag};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -154,6 +155,8 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
       {(void**)&c->partial, sizeof(double) * 3 * (c->plan.n1 / 2 + 1) * W},
       {(void**)&c->status, sizeof(int32_t) * W},
       {(void**)&c->tdi_tiles, sizeof(lisa::TdiTileTerm) * ((n + lisa::kTdiTile - 1) / lisa::kTdiTile) * 42},
+      {(void**)&c->tdi_pairs, sizeof(lisa::TdiTilePair) * ((n + lisa::kTdiTile - 1) / lisa::kTdiTile) * lisa::kTdiPairs},
+      {(void**)&c->tdi_flag, sizeof(int)},
   };
   for (auto& a : allocs) {
     cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -178,11 +181,18 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
   if (e == cudaSuccess) e = lisa::launch_psd_weights(c, s);
   if (e == cudaSuccess) e = lisa::launch_twiddles(c, s);
   if (e == cudaSuccess) e = lisa::launch_tdi_tiles(c, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->tdi_flag, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = lisa::launch_tdi_pairs(c, s);
+  int wide = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&wide, c->tdi_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_ctx(c);
     return cuda_fail(e, "lisa_td_create");
   }
+  // the combined-FIR TDI kernel runs when every pair fits (grids of a few
+  // seconds' spacing); finer grids keep one FIR per term
+  c->tdi_comb = wide ? 0 : 1;
   *out = c;
   return LISA_TD_OK;
 }

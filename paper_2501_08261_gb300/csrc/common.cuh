@@ -94,7 +94,7 @@ struct WalkerRec {
   double c2psi, s2psi;
   // precession stand-in
   double S, ctilt, stilt, kp, u_ref, G_ref, gamma_ref;
-  double q03[4];      // J->L0 inverse-conjugate quaternion times q(phi_ref, iota, 0)
+  double q03[4];      // inverse of the J->L0 quaternion times q(phi_ref, iota, 0)
   ModeRec mode[kNMode];
   int nmode;
   int status;         // 0 ok, 1 invalid parameters
@@ -152,6 +152,33 @@ struct alignas(16) TdiTileTerm {
   int split;             // the fraction leaves [0, 1) inside the tile
   float sa1, sa2, se;    // sign * a1, sign * a2, sign * eps_a
   int pad[3];
+};
+
+// ---- mixed-path TDI: one FIR per (channel, link) pair -----------------------
+// The terms of one channel that read the same link differ only in their
+// delays, and each is linear in the first differences dy of that link, so
+// per tile their difference weights add into one FIR over the union of their
+// windows: G[k] multiplies dy at row (output row + boff + k).  G is summed in
+// FP64 and rounded to FP32 once.  The zeroth and first moments of that
+// rounding error are taken out by two one-tap corrections wa, wb at the
+// centre rows (offsets ma < mb) of the pair's outermost terms, so the error
+// left in the FIR's response vanishes to second order in frequency.
+// Each term keeps its own |y|-sized centre sample, its linear-interpolation
+// part and the drift of its fraction (TdiTermLite); terms whose fraction wraps
+// inside the tile (kind 2) are evaluated per sample and stay out of G.
+constexpr int kTdiPairs = 12;           // 6 links x the 2 channels that read each
+constexpr int kGMax = 64;               // widest combined FIR (taps)
+struct TdiTermLite {
+  int bo, kind;          // centre offset; 0 undelayed, 1 in G, 2 per-sample
+  float sg, se, sa1, sa2;
+  float eps_a, a1, a2;   // unsigned fraction and drift (kind 2)
+};
+struct alignas(16) TdiTilePair {
+  float G[kGMax];        // signed combined weights, zero beyond ntap
+  int boff, ntap4, ma, mb;
+  int chan, nterm;
+  float wa, wb;
+  TdiTermLite t[4];
 };
 
 // ---- small helpers --------------------------------------------------------

@@ -37,6 +37,9 @@ struct lisa_td_ctx {
   int* chan_list;                  // device [3]: indices of the channels in the mask
   lisa::TdiTileTerm* tdi_tiles;    // mixed path: [n / 64 tiles][delayed terms]
   int n_dterms;                    // delayed terms (18 for TDI 1.5, 42 for TDI 2)
+  lisa::TdiTilePair* tdi_pairs;    // mixed path: [n / 64 tiles][kTdiPairs] combined FIRs
+  int tdi_comb;                    // 1: every pair's FIR fits kGMax taps (tdi_comb_kernel)
+  int* tdi_flag;                   // device word: set when a pair is wider than kGMax
   double* data64;                  // [3][n]
   float* data32;                   // [3][n]
   int has_data;
@@ -114,5 +117,8 @@ cudaError_t run_loglike_stages(const lisa_td_ctx* c, const double* params, int W
                                int32_t* status, cudaStream_t s, cudaEvent_t* ev);
 TdiTable build_tdi_table(int gen);
 cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s);
+// combined per-(channel, link) FIR weights of the mixed TDI; sets *c->tdi_flag
+// when a pair needs more than kGMax taps
+cudaError_t launch_tdi_pairs(const lisa_td_ctx* c, cudaStream_t s);
 
 }  // namespace lisa

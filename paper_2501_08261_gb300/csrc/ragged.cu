@@ -190,6 +190,7 @@ cudaError_t get_view(lisa_td_ctx* c, Ragged* r, int64_t nv, cudaStream_t s, View
     v.orb64 = c->orb64 + vw->off;
     v.orb32 = c->orb32 + vw->off;
     v.tdi_tiles = c->tdi_tiles + (vw->off / kTdiTile) * c->n_dterms;
+    v.tdi_pairs = c->tdi_pairs + (vw->off / kTdiTile) * kTdiPairs;
     v.prof_ev = nullptr;
     v.prof_on = 0;
     v.ragged = nullptr;

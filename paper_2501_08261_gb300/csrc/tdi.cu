@@ -283,17 +283,13 @@ __device__ void lagrange_weights_f64(double eps, int K, double* w) {
   }
 }
 
-__global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
-                                 const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
-                                 int ntiles, int nested, TdiTileTerm* __restrict__ out) {
-  const int nd = tab->n_dterms;
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (int64_t)ntiles * nd) return;
-  const int tile = (int)(id / nd), d = (int)(id % nd);
-  int jl = 0, q = 0;
-  for (int j = 0; j < kNLink; ++j)
-    for (int qq = 0; qq < tab->nterm[j]; ++qq)
-      if (tab->dterm[j][qq] == d) { jl = j; q = qq; }
+// Tile record of delayed term (jl, q) for the tile starting at sample
+// tile * kTdiTile; cs[0 .. K-2] receives the signed FP64 difference weights
+// (the centre one without the linear part eps_a, which the kernels add
+// exactly), whose FP32 roundings are R.C.
+__device__ void build_tile_term(const TdiTable* __restrict__ tab,
+                                const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
+                                int tile, int jl, int q, int nested, TdiTileTerm& R, double* cs) {
   const TdiTerm T = tab->term[jl][q];
   const int64_t ia = (int64_t)tile * kTdiTile;
   auto tau_rel = [&](int j) -> double {          // tau(i) - i at i = ia + j
@@ -303,7 +299,6 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
   const double ta = tau_rel(0);
   const double fl = floor(ta);
   const double eps = ta - fl;
-  TdiTileTerm R;
   R.bo = (int)fl;
   R.eps_a = (float)eps;
   // quadratic drift through j = 0, 32, 63
@@ -321,8 +316,9 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
   double w[32];
   lagrange_weights_f64(eps, K, w);
   const int H = (K - 2) / 2;                       // node offsets o_k = k - H, k = 0..K-1
+  const double sgd = (double)T.sign;
   double mom = 0.0;
-  for (int q = 0; q < 32; ++q) R.C[q] = 0.0f;
+  for (int q2 = 0; q2 < 32; ++q2) R.C[q2] = 0.0f;
   for (int mi = 0; mi < K - 1; ++mi) {             // m = mi - H, from -H to H
     const int m = mi - H;
     double c = 0.0;
@@ -334,24 +330,138 @@ __global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
     if (m == 0) {
       // the linear-interpolation part eps_a dy_c goes to the compensated main
       // accumulator in the kernel; the table keeps the remainder
-      const float cf = (float)(c - (double)R.eps_a);
+      const double rem = c - (double)R.eps_a;
+      const float cf = (float)rem;
       R.C[mi] = cf;
+      cs[mi] = sgd * rem;
       mom += ((double)R.eps_a + (double)cf) - c;
     } else {
       const float cf = (float)c;
       R.C[mi] = cf;
+      cs[mi] = sgd * c;
       mom += (double)cf - c;
     }
   }
   // the term's sign, exact on every field that the kernel only adds
   const float sg = (float)T.sign;
-  for (int q = 0; q < 32; ++q) R.C[q] *= sg;
+  for (int q2 = 0; q2 < 32; ++q2) R.C[q2] *= sg;
   R.m1 = sg * (float)mom;
   R.sa1 = sg * R.a1;
   R.sa2 = sg * R.a2;
   R.se = sg * R.eps_a;
   R.pad[0] = R.pad[1] = R.pad[2] = 0;
+}
+
+__global__ void tdi_tiles_kernel(const TdiTable* __restrict__ tab,
+                                 const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
+                                 int ntiles, int nested, TdiTileTerm* __restrict__ out) {
+  const int nd = tab->n_dterms;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)ntiles * nd) return;
+  const int tile = (int)(id / nd), d = (int)(id % nd);
+  int jl = 0, q = 0;
+  for (int j = 0; j < kNLink; ++j)
+    for (int qq = 0; qq < tab->nterm[j]; ++qq)
+      if (tab->dterm[j][qq] == d) { jl = j; q = qq; }
+  TdiTileTerm R;
+  double cs[32];
+  build_tile_term(tab, orb, n, dt, K, tile, jl, q, nested, R, cs);
   out[id] = R;
+}
+
+// channel of pair (link j, k-th channel reading link j in term order), or -1
+__host__ __device__ inline int pair_channel(const TdiTable* tab, int j, int k) {
+  int seen[3] = {-1, -1, -1}, ns = 0;
+  for (int q = 0; q < tab->nterm[j]; ++q) {
+    const int ch = tab->term[j][q].chan;
+    bool dup = false;
+    for (int u = 0; u < ns; ++u) dup = dup || seen[u] == ch;
+    if (!dup && ns < 3) seen[ns++] = ch;
+  }
+  return k < ns ? seen[k] : -1;
+}
+
+// One thread per (tile, pair): the pair's terms and their combined FIR.
+__global__ void tdi_pairs_kernel(const TdiTable* __restrict__ tab,
+                                 const OrbitRec64* __restrict__ orb, int64_t n, double dt, int K,
+                                 int ntiles, int nested, TdiTilePair* __restrict__ out,
+                                 int* __restrict__ too_wide) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)ntiles * kTdiPairs) return;
+  const int tile = (int)(id / kTdiPairs), pj = (int)(id % kTdiPairs);
+  const int j = pj / 2, ch = pair_channel(tab, j, pj % 2);
+  const int H = (K - 2) / 2;
+  TdiTilePair P;
+  memset(&P, 0, sizeof(P));
+  P.chan = ch < 0 ? 0 : ch;
+  double g[kGMax];
+  for (int k = 0; k < kGMax; ++k) g[k] = 0.0;
+  double cs[4][32];
+  int first = -1, bmin = 0, bmax = 0, cmin = 0, cmax = 0;
+  for (int q = 0; q < tab->nterm[j] && ch >= 0; ++q) {
+    const TdiTerm T = tab->term[j][q];
+    if (T.chan != ch || P.nterm >= 4) continue;
+    TdiTermLite& L = P.t[P.nterm];
+    L.sg = (float)T.sign;
+    if (T.ndelay == 0) {
+      L.kind = 0;
+      L.bo = 0;
+    } else {
+      TdiTileTerm R;
+      build_tile_term(tab, orb, n, dt, K, tile, j, q, nested, R, cs[P.nterm]);
+      L.bo = R.bo;
+      L.kind = R.split ? 2 : 1;
+      L.se = R.se;
+      L.sa1 = R.sa1;
+      L.sa2 = R.sa2;
+      L.eps_a = R.eps_a;
+      L.a1 = R.a1;
+      L.a2 = R.a2;
+      if (!R.split) {
+        const int b = R.bo - H;
+        if (first < 0) {
+          first = P.nterm;
+          bmin = bmax = b;
+          cmin = cmax = R.bo;
+        }
+        bmin = b < bmin ? b : bmin;
+        bmax = b > bmax ? b : bmax;
+        cmin = R.bo < cmin ? R.bo : cmin;
+        cmax = R.bo > cmax ? R.bo : cmax;
+      }
+    }
+    P.nterm++;
+  }
+  if (first >= 0) {
+    const int ntap = bmax - bmin + K - 1;
+    if (ntap > kGMax) {
+      atomicOr(too_wide, 1);
+    } else {
+      for (int u = 0; u < P.nterm; ++u) {
+        if (P.t[u].kind != 1) continue;
+        const int o = P.t[u].bo - H - bmin;
+        for (int m = 0; m < K - 1; ++m) g[o + m] += cs[u][m];
+      }
+      // zeroth and first moments (rows relative to the output row) of the
+      // rounding error, cancelled by taps at the outermost centre rows
+      double s0 = 0.0, s1 = 0.0;
+      for (int k = 0; k < kGMax; ++k) {
+        P.G[k] = (float)g[k];
+        const double e = (double)P.G[k] - g[k];
+        s0 += e;
+        s1 += e * (double)(bmin + k);
+      }
+      const int ka = cmin, kb = cmax > cmin ? cmax : cmin + 1;
+      const double wb = (s0 * (double)ka - s1) / (double)(kb - ka);
+      P.wa = (float)(-s0 - wb);
+      P.wb = (float)wb;
+      P.ma = ka;
+      P.mb = kb;
+      P.boff = bmin;
+      P.ntap4 = (ntap + 3) & ~3;
+    }
+  }
+  out[id] = P;
 }
 
 constexpr int kMixTile = kTdiTile;
@@ -446,8 +556,8 @@ __device__ __forceinline__ void apply_tile_term(f2 (&main)[SPT], f2 (&acc)[SPT],
 
 // tiles whose fraction wraps inside the tile (rare): per-sample FP32 weights,
 // still as y_c' + sum w_k (y_k - y_c') so that their DC error meets only differences
-template <int K>
-__device__ __noinline__ float4 split_one(const float2* __restrict__ yw, const TdiTileTerm* P,
+template <int K, typename Rec>
+__device__ __noinline__ float4 split_one(const float2* __restrict__ yw, const Rec* P,
                                          int s, int hl, int rows, int lane) {
   const int H = (K - 2) / 2;
   const float jj = (float)s;
@@ -615,6 +725,188 @@ __global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_mixed_kernel(
   }
 }
 
+// The terms of one (channel, link) pair (TdiTilePair): per term its centre
+// sample (compensated), its linear-interpolation part (exact product,
+// compensated) and the drift of its fraction; then the pair's combined FIR on
+// the differences and its two moment corrections.
+template <int K, int SPT>
+__device__ __forceinline__ void apply_pair(f2 (&main)[SPT], f2 (&acc)[SPT],
+                                           const float2* __restrict__ yw,
+                                           const float2* __restrict__ dyw, const TdiTilePair& P,
+                                           int s0, int hl, int rows, int lane) {
+  const int base = s0 + hl;
+  for (int q = 0; q < P.nterm; ++q) {
+    const TdiTermLite& T = P.t[q];
+    if (T.kind == 0) {
+      add_rows<SPT>(main, acc, yw, base, T.sg, lane);
+      continue;
+    }
+    if (T.kind == 2) {
+#pragma unroll
+      for (int r = 0; r < SPT; ++r) {
+        const float4 v = split_one<K>(yw, &T, s0 + r, hl, rows, lane);
+        acc2(main[r].x, acc[r].x, T.sg * v.x);
+        acc2(main[r].y, acc[r].y, T.sg * v.y);
+        acc[r].x = fmaf(T.sg, v.z, acc[r].x);
+        acc[r].y = fmaf(T.sg, v.w, acc[r].y);
+      }
+      continue;
+    }
+    const int c0 = base + T.bo;
+    add_rows<SPT>(main, acc, yw, c0, T.sg, lane);
+    const float se = T.se, a1 = T.sa1, a2 = T.sa2;
+#pragma unroll
+    for (int r = 0; r < SPT; ++r) {
+      const f2 d = ld2(&dyw[(c0 + r) * kPW2 + lane]);
+      const float jj = (float)(s0 + r);
+      const float dr = jj * fmaf(jj, a2, a1);
+      acc[r].x = fmaf(dr, d.x, acc[r].x);
+      acc[r].y = fmaf(dr, d.y, acc[r].y);
+      const float px = se * d.x, py = se * d.y;
+      const float ex = fmaf(se, d.x, -px), ey = fmaf(se, d.y, -py);
+      acc2(main[r].x, acc[r].x, px);
+      acc2(main[r].y, acc[r].y, py);
+      acc[r].x += ex;
+      acc[r].y += ey;
+    }
+  }
+  const int nt4 = P.ntap4;
+  if (nt4 == 0) return;
+  {
+    const int ca = base + P.ma, cb = base + P.mb;
+    const float wa = P.wa, wb = P.wb;
+#pragma unroll
+    for (int r = 0; r < SPT; ++r) {
+      const f2 da = ld2(&dyw[(ca + r) * kPW2 + lane]);
+      const f2 db = ld2(&dyw[(cb + r) * kPW2 + lane]);
+      acc[r].x = fmaf(wa, da.x, fmaf(wb, db.x, acc[r].x));
+      acc[r].y = fmaf(wa, da.y, fmaf(wb, db.y, acc[r].y));
+    }
+  }
+  const int b0 = base + P.boff;
+  f2 win[SPT];
+#pragma unroll
+  for (int r = 0; r < SPT; ++r) win[r] = ld2(&dyw[(b0 + r) * kPW2 + lane]);
+  const float4* G4 = reinterpret_cast<const float4*>(P.G);
+#pragma unroll 1
+  for (int k = 0; k < nt4; k += 4) {
+    const float4 g = G4[k >> 2];
+    const float gk[4] = {g.x, g.y, g.z, g.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+#pragma unroll
+      for (int r = 0; r < SPT; ++r) {
+        acc[r].x = fmaf(gk[u], win[r].x, acc[r].x);
+        acc[r].y = fmaf(gk[u], win[r].y, acc[r].y);
+      }
+#pragma unroll
+      for (int r = 0; r < SPT - 1; ++r) win[r] = win[r + 1];
+      win[SPT - 1] = ld2(&dyw[(b0 + SPT + k + u) * kPW2 + lane]);
+    }
+  }
+}
+
+// Mixed TDI with one combined FIR per (channel, link) pair: the CTA shape,
+// staging, accumulators and A, E, T epilogue of tdi_mixed_kernel.
+template <int K>
+__global__ void __launch_bounds__(32 * kMixWarps, 1) tdi_comb_kernel(
+    const TdiTilePair* __restrict__ pairs, int W, int ldw, int64_t n, const float* __restrict__ y,
+    float* __restrict__ out, const float* __restrict__ data, int resid, int hl, int hr,
+    const int64_t* __restrict__ woff) {
+  constexpr int SPT = kMixSpt;
+  extern __shared__ float2 smem2[];
+  const int rows = kMixTile + hl + hr;
+  float2* ybuf0 = smem2;                           // [rows][kPW2], links 0, 2, 4
+  float2* ybuf1 = smem2 + rows * kPW2;             // links 1, 3, 5
+  float2* dyw = smem2 + 2 * rows * kPW2;           // dy_r = y_{r+1} - y_r of the current link
+  __shared__ TdiTilePair pp[kTdiPairs];
+  const int lane = threadIdx.x, warp = threadIdx.y;
+  const int tid = warp * 32 + lane;
+  const int64_t i0 = (int64_t)blockIdx.x * kMixTile;
+  const int wa = blockIdx.y * 64 + 2 * lane;       // walkers wa, wa + 1
+  const int s0 = warp * SPT;
+  if (woff && group_inactive(woff + blockIdx.y * 64, 64, i0 + kMixTile)) return;
+  const int64_t lo_a = woff ? woff[wa] : 0, lo_b = woff ? woff[wa + 1] : 0;
+  {
+    const int4* src = reinterpret_cast<const int4*>(pairs + (int64_t)blockIdx.x * kTdiPairs);
+    int4* dst = reinterpret_cast<int4*>(pp);
+    const int words = kTdiPairs * (int)(sizeof(TdiTilePair) / sizeof(int4));
+    for (int q = tid; q < words; q += 32 * kMixWarps) dst[q] = src[q];
+  }
+  f2 mx[SPT], my[SPT], mz[SPT], sx[SPT], sy[SPT], sz[SPT];
+#pragma unroll
+  for (int r = 0; r < SPT; ++r)
+    mx[r] = my[r] = mz[r] = sx[r] = sy[r] = sz[r] = f2{0.0f, 0.0f};
+
+  auto stage = [&](int j, float2* dst) {
+    for (int r = warp; r < rows; r += kMixWarps) {
+      const int64_t g = i0 - hl + r;
+      float* d = reinterpret_cast<float*>(dst + r * kPW2 + lane);
+      const bool in = g >= 0 && g < n;
+      const float* src = in ? y + ((int64_t)j * n + g) * ldw + wa : y;
+      if (in && g >= lo_a && wa < W) cp_async4(d, src); else d[0] = 0.0f;
+      if (in && g >= lo_b && wa + 1 < W) cp_async4(d + 1, src + 1); else d[1] = 0.0f;
+    }
+    cp_async_commit();
+  };
+  stage(0, ybuf0);
+  for (int j = 0; j < kNLink; ++j) {
+    float2* yw = (j & 1) ? ybuf1 : ybuf0;
+    if (j + 1 < kNLink) {
+      stage(j + 1, (j & 1) ? ybuf0 : ybuf1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    for (int r = warp; r < rows; r += kMixWarps) {
+      float2 a = yw[r * kPW2 + lane];
+      float2 b = r + 1 < rows ? yw[(r + 1) * kPW2 + lane] : a;
+      dyw[r * kPW2 + lane] = make_float2(b.x - a.x, b.y - a.y);
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      const TdiTilePair& P = pp[2 * j + k];
+      if (P.nterm == 0) continue;
+      if (P.chan == 0) apply_pair<K, SPT>(mx, sx, yw, dyw, P, s0, hl, rows, lane);
+      else if (P.chan == 1) apply_pair<K, SPT>(my, sy, yw, dyw, P, s0, hl, rows, lane);
+      else apply_pair<K, SPT>(mz, sz, yw, dyw, P, s0, hl, rows, lane);
+    }
+    __syncthreads();                               // link j's buffers are free again
+  }
+  const float r2 = 0.70710678118654752f, r6 = 0.40824829046386302f, r3 = 0.57735026918962576f;
+#pragma unroll
+  for (int r = 0; r < SPT; ++r) {
+    const int64_t i = i0 + s0 + r;
+    if (i >= n) continue;
+    float dA = 0.0f, dE = 0.0f, dT = 0.0f;
+    if (resid) {
+      dA = data[i];
+      dE = data[n + i];
+      dT = data[2 * n + i];
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int w = wa + e;
+      if (w >= W || i < (e ? lo_b : lo_a)) continue;
+      const float Mx = e ? mx[r].y : mx[r].x, My = e ? my[r].y : my[r].x, Mz = e ? mz[r].y : mz[r].x;
+      const float Sx = e ? sx[r].y : sx[r].x, Sy = e ? sy[r].y : sy[r].x, Sz = e ? sz[r].y : sz[r].x;
+      df32 zx = two_sum(Mz, -Mx);
+      df32 xy = two_sum(Mx, -2.0f * My);
+      df32 xyz = two_sum(xy.hi, Mz);
+      df32 xy3 = two_sum(Mx, My);
+      df32 t3 = two_sum(xy3.hi, Mz);
+      const float A = zx.hi + (zx.lo + (Sz - Sx));
+      const float E = xyz.hi + ((xy.lo + xyz.lo) + (Sx - 2.0f * Sy + Sz));
+      const float Tt = t3.hi + ((xy3.lo + t3.lo) + (Sx + Sy + Sz));
+      out[(0 * n + i) * ldw + w] = A * r2 - dA;
+      out[(1 * n + i) * ldw + w] = E * r6 - dE;
+      out[(2 * n + i) * ldw + w] = Tt * r3 - dT;
+    }
+  }
+}
+
 template <int K>
 cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* out, int resid,
                      cudaStream_t s, int nd) {
@@ -641,9 +933,20 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* y, void* 
     cudaFuncSetAttribute(tdi_mixed_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     dim3 blockm(32, kMixTile / kMixSpt);
-    tdi_mixed_kernel<K><<<gridm, blockm, smem, s>>>(c->tdi_tab, c->tdi_tiles, W, ldw, c->n,
+    if (c->tdi_comb) {
+      // the combined FIR reads up to 3 zero-weight taps past a pair's window
+      const int hrc = hrm + 4;
+      const size_t smc = (size_t)3 * (kMixTile + hlm + hrc) * kPW2 * sizeof(float2);
+      cudaFuncSetAttribute(tdi_comb_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smc);
+      tdi_comb_kernel<K><<<gridm, blockm, smc, s>>>(c->tdi_pairs, W, ldw, c->n,
                                                    (const float*)y, (float*)out, c->data32,
-                                                   resid, hlm, hrm, c->woff);
+                                                   resid, hlm, hrc, c->woff);
+    } else {
+      tdi_mixed_kernel<K><<<gridm, blockm, smem, s>>>(c->tdi_tab, c->tdi_tiles, W, ldw, c->n,
+                                                     (const float*)y, (float*)out, c->data32,
+                                                     resid, hlm, hrm, c->woff);
+    }
   }
   return cudaGetLastError();
 }
@@ -656,6 +959,15 @@ cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s) {
   tdi_tiles_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
       c->tdi_tab, c->orb64, c->n, c->cfg.dt, c->cfg.lagrange_order + 1, ntiles,
       c->cfg.tdi_nested, c->tdi_tiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tdi_pairs(const lisa_td_ctx* c, cudaStream_t s) {
+  const int ntiles = (int)((c->n + kTdiTile - 1) / kTdiTile);
+  const int64_t m = (int64_t)ntiles * kTdiPairs;
+  tdi_pairs_kernel<<<(unsigned)((m + 127) / 128), 128, 0, s>>>(
+      c->tdi_tab, c->orb64, c->n, c->cfg.dt, c->cfg.lagrange_order + 1, ntiles,
+      c->cfg.tdi_nested, c->tdi_pairs, c->tdi_flag);
   return cudaGetLastError();
 }
 

@@ -70,9 +70,12 @@ def test_mixed_projection(name):
             assert np.max(np.abs(y[j, :, w] - yo[l])) <= TOL * scale, (w, l)
 
 
-@pytest.mark.parametrize("gen,orbit", [(15, 0), (20, 1)])
-def test_mixed_tdi_of_oracle_links(gen, orbit):
-    cfg = workloads.config("c1_fp64_1d", tdi_gen=gen, orbit=orbit, n=4320)
+# dt = 5 s runs the kernel with one combined FIR per (channel, link); at
+# dt = 1 s the terms of a pair spread over more than 64 taps, so the kernel
+# with one FIR per term runs
+@pytest.mark.parametrize("gen,orbit,dt", [(15, 0, 5.0), (20, 1, 5.0), (15, 0, 1.0), (20, 1, 1.0)])
+def test_mixed_tdi_of_oracle_links(gen, orbit, dt):
+    cfg = workloads.config("c1_fp64_1d", tdi_gen=gen, orbit=orbit, n=4320, dt=dt)
     s = oracle_setup(cfg)
     rng = np.random.default_rng(5)
     W = 70                                        # two CTA walker blocks, ragged
