@@ -57,7 +57,9 @@ typedef struct {
   int32_t tdi_gen;         /* 15 (X_1.5) or 20 (X_2)                             */
   int32_t channel_mask;    /* bit0 A, bit1 E, bit2 T (Sec. III.D: A, AE, AET)   */
   int32_t lagrange_order;  /* odd p in {1, 3, 5, ..., 31}; 1 = linear (Sec. II.B) */
-  int32_t orbit_kind;      /* 0 rigid equal-arm, 1 Keplerian unequal-arm         */
+  int32_t orbit_kind;      /* 0 rigid equal-arm, 1 Keplerian unequal-arm, 2 the
+                            * caller's table of spacecraft positions
+                            * (lisa_td_create_orbits)                            */
   int32_t mode_mask;       /* bits (2,2),(2,1),(3,3),(3,2),(4,4) (Sec. II.A)     */
   int32_t precessing;      /* 0 aligned spins, 1 precessing twist-up             */
   int32_t precision;       /* 0 FP64, 1 mixed                                    */
@@ -73,8 +75,41 @@ typedef struct {
 /* Create a context: validates cfg, builds the orbit tables (one kernel, FP64),
  * the PSD weights of the band bins and the FFT plan, and allocates the
  * workspace for cfg->max_walkers walkers.  Sec. II.B: the orbit quantities
- * are computed once, not per likelihood call.  On error *out is set to NULL. */
+ * are computed once, not per likelihood call.  On error *out is set to NULL
+ * and everything allocated so far is freed; LISA_TD_ENOMEM when a device
+ * allocation fails.  With the environment variable LISA_TD_FAIL_ALLOC=k the
+ * k-th workspace allocation (0-based) fails that way on purpose (host-side
+ * fault injection for testing the clean-up path). */
 int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream);
+
+/* Spacecraft positions supplied by the caller, e.g. a mission orbit file such
+ * as the one the paper's unequal-arm runs use (Sec. II.B, orbits; Sec. III.C).
+ * Row j holds the three spacecraft's positions at time t0 + j dt:
+ * pos_host[(j * 3 + k) * 3 + d] = coordinate d (x, y, z) of spacecraft k + 1,
+ * in metres, in the solar-system-barycentric ecliptic frame.  The table must
+ * cover the grid and the light times before it: t0 <= grid t0 - 120 s and
+ * t0 + (rows - 1) dt >= last grid time; rows >= 8.  The library resamples it
+ * with the centred 8-point Lagrange interpolant in the row index (nodes
+ * j - 3 .. j + 4 around floor((t - t0) / dt), shifted inwards at the table's
+ * ends), solves each light time from |r_r(t) - r_s(t - L)| = c L by
+ * fixed-point iteration, and takes emission positions at t - L, as for the
+ * built-in orbit models.  The mixed path stores positions as FP32 offsets
+ * from a guiding centre on the 1 AU circle turning at the sidereal rate, with
+ * its phase fitted to the table; tables whose barycentre leaves that circle
+ * by more than 0.1 AU are refused (LISA_TD_ERANGE) for precision 1. */
+typedef struct {
+  double t0;               /* time of row 0 [s]                                  */
+  double dt;               /* row spacing [s], > 0                               */
+  int64_t rows;            /* rows in the table                                  */
+  const double* pos_host;  /* [rows][3][3] positions [m]; copied, not kept       */
+} lisa_td_orbit_table;
+
+/* lisa_td_create for cfg->orbit_kind == 2: the orbit tables are built from
+ * the caller's positions (lisa_td_orbit_table).  LISA_TD_EINVAL when
+ * orbit_kind is not 2, the table is NULL, too short or does not cover the
+ * grid. */
+int lisa_td_create_orbits(lisa_td_ctx** out, const lisa_td_config* cfg,
+                          const lisa_td_orbit_table* orbits, void* stream);
 
 /* Store the data d (A, E, T time series; FP64 device [3][n], row c = A,E,T).
  * Sec. II.C: zero-noise injections, so d is normally an injected template.
@@ -167,6 +202,16 @@ int lisa_td_autotune(lisa_td_ctx* ctx, const double* params_dev, int32_t W,
 #define LISA_TD_PROF_CALLS 256
 int lisa_td_profile(lisa_td_ctx* ctx, int32_t enable);
 int lisa_td_profile_read(lisa_td_ctx* ctx, double* stage_ms, int64_t* calls);
+
+/* FP32 FMA rate of the current device (measurement support, no paper
+ * counterpart): the denominator of the mixed path's roofline, measured in the
+ * caller's process and on its clocks.  Runs a grid of 4 CTAs x 512 threads per
+ * SM, each thread 16 independent FMA chains of 16384 steps, four times on
+ * `stream` (the first untimed), and writes the best rate in TFLOP/s (2 flops
+ * per FMA) to *tflops_host.  Synchronises `stream`; allocates (and frees) a
+ * small stream-ordered buffer.  LISA_TD_EINVAL for a NULL pointer,
+ * LISA_TD_ECUDA when a CUDA call fails. */
+int lisa_td_fp32_fma_rate(double* tflops_host, void* stream);
 
 /* No-allocation variant of the DFT + PSD-weighted norm stages.  The paper has
  * no counterpart: this is a service for callers that must not allocate device

@@ -77,12 +77,49 @@ def kepler_position(craft, t):
     return np.stack([x, y, zt], axis=-1)
 
 
+class OrbitTable:
+    """Spacecraft positions given as a table, the form of a mission orbit file
+    (Sec. II.B needs the positions at every time of the observation; Sec. III.C
+    runs on such a file).  Row j holds the three spacecraft's positions [m] at
+    time t0 + j dt; pos_m has shape [rows][3][3] (row, spacecraft 1..3, x y z).
+
+    Positions at other times (declared reading: the paper does not say how it
+    resamples its orbit file): the degree-7 Lagrange polynomial through the
+    eight rows j - 3 .. j + 4 around j = floor((t - t0) / dt), the eight rows
+    moved inwards where they would leave the table."""
+
+    def __init__(self, t0, dt, pos_m):
+        self.t0 = float(t0)
+        self.dt = float(dt)
+        self.pos = np.asarray(pos_m, dtype=np.float64) / K.C_SI   # light-seconds
+        if self.pos.ndim != 3 or self.pos.shape[1:] != (3, 3) or self.pos.shape[0] < 8:
+            raise ValueError("orbit table must be [rows >= 8][3][3]")
+
+    def position(self, craft, t):
+        t = np.asarray(t, dtype=np.float64)
+        x = (t - self.t0) / self.dt
+        rows = self.pos.shape[0]
+        first = np.clip(np.floor(x).astype(np.int64) - 3, 0, rows - 8)
+        u = x - first                                   # in units of rows, nodes 0..7
+        out = np.zeros(t.shape + (3,))
+        for k in range(8):
+            w = np.ones_like(u)
+            for m in range(8):
+                if m != k:
+                    w = w * (u - m) / (k - m)
+            out = out + w[..., None] * self.pos[first + k, craft - 1, :]
+        return out
+
+
 def position(kind, craft, t):
     """Position of ``craft`` at times t for orbit model ``kind``.
 
     Besides "rigid" and "kepler", two frozen constellations serve the closed-form
     pins: "static_rigid" (the rigid triangle at t = 0, equal arms) and
-    "static_kepler" (the Keplerian positions at t = 0, unequal arms)."""
+    "static_kepler" (the Keplerian positions at t = 0, unequal arms); an
+    ``OrbitTable`` gives the caller's positions."""
+    if isinstance(kind, OrbitTable):
+        return kind.position(craft, t)
     if kind == "rigid":
         return rigid_position(craft, t)
     if kind == "kepler":
@@ -98,10 +135,10 @@ def position(kind, craft, t):
 def light_time(kind, link, t, iters=8):
     """Light travel time L_l(t) [s] of link ``link`` for reception at time t."""
     t = np.asarray(t, dtype=np.float64)
-    if kind in ("rigid", "static_rigid"):
+    if isinstance(kind, str) and kind in ("rigid", "static_rigid"):
         return np.full(t.shape, K.ARM_S)
     s, r = LINK_ENDS[link]
-    if kind == "static_kepler":
+    if isinstance(kind, str) and kind == "static_kepler":
         return np.full(t.shape, float(np.linalg.norm(position(kind, r, 0.0)
                                                      - position(kind, s, 0.0))))
     rr = position(kind, r, t)

@@ -22,7 +22,7 @@ class Setup:
     tdi_gen: int = 15
     channel_mask: int = 7
     lagrange_order: int = 31
-    orbit: str = "rigid"          # "rigid" | "kepler"
+    orbit: object = "rigid"       # "rigid" | "kepler" | an orbits.OrbitTable
     mode_mask: int = 1            # bit0 (2,2) .. bit4 (4,4)
     precessing: bool = False
     tdi_nested: bool = False      # TDI delays as nested operator products

@@ -12,13 +12,14 @@ from . import build as _build
 
 LISA_TD_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
-EXPORTS = ("lisa_td_create", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
+EXPORTS = ("lisa_td_create", "lisa_td_create_orbits", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
+           "lisa_td_fp32_fma_rate",
            "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune", "lisa_td_noise",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
            "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept", "lisa_pt_swap",
-           "flow_create", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
+           "flow_create", "flow_set_wait_limit", "flow_nparams", "flow_set_params", "flow_get_params", "flow_set_frame",
            "flow_logprob", "flow_propose", "flow_grad", "flow_adam", "flow_train", "flow_destroy")
 NSTAGE = 7
 STAGES = ("prep", "waveform", "project", "tdi", "fft_pass1", "fft_pass2_norm", "reduce")
@@ -35,6 +36,12 @@ class Config(ctypes.Structure):
                 ("tdi_nested", ctypes.c_int32)]
 
 
+class OrbitTable(ctypes.Structure):
+    """Mirror of lisa_td_orbit_table."""
+    _fields_ = [("t0", ctypes.c_double), ("dt", ctypes.c_double), ("rows", ctypes.c_int64),
+                ("pos_host", ctypes.c_void_p)]
+
+
 def load_library(path=None):
     path = path or _build.LIB
     if not os.path.exists(path):
@@ -44,6 +51,8 @@ def load_library(path=None):
     P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
     sig = {
         "lisa_td_create": ([ctypes.POINTER(P), ctypes.POINTER(Config), P], ctypes.c_int),
+        "lisa_td_create_orbits": ([ctypes.POINTER(P), ctypes.POINTER(Config),
+                                   ctypes.POINTER(OrbitTable), P], ctypes.c_int),
         "lisa_td_set_data": ([P, P, P], ctypes.c_int),
         "lisa_td_waveform": ([P, P, I32, P, P], ctypes.c_int),
         "lisa_td_project": ([P, P, I32, P, P], ctypes.c_int),
@@ -57,6 +66,7 @@ def load_library(path=None):
         "lisa_td_profile_read": ([P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)],
                                  ctypes.c_int),
         "lisa_td_residual_loglike_noalloc": ([ctypes.POINTER(Config), P, I32, P, P], ctypes.c_int),
+        "lisa_td_fp32_fma_rate": ([ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
         "lisa_fisher_npoints": ([I32], ctypes.c_int),
         "lisa_fisher_points": ([P, P, P, I32, P, P], ctypes.c_int),
         "lisa_fisher_assemble": ([P, P, I32, P, P], ctypes.c_int),
@@ -68,6 +78,7 @@ def load_library(path=None):
         "lisa_pt_swap": ([I32, I32, P, P, P, P, P, P, P], ctypes.c_int),
         "flow_create": ([ctypes.POINTER(P), I32, I32, I32, I32, P, P, P], ctypes.c_int),
         "flow_nparams": ([P, ctypes.POINTER(I64)], ctypes.c_int),
+        "flow_set_wait_limit": ([P, I64], ctypes.c_int),
         "flow_set_params": ([P, P, P], ctypes.c_int),
         "flow_get_params": ([P, P, P], ctypes.c_int),
         "flow_set_frame": ([P, P, P, P], ctypes.c_int),
@@ -130,6 +141,20 @@ def lisa_td_create(cfg, stream=None):
     h = ctypes.c_void_p()
     _check(lib().lisa_td_create(ctypes.byref(h), ctypes.byref(cfg), _stream(stream)),
            "lisa_td_create")
+    return h
+
+
+def lisa_td_create_orbits(cfg, t0, dt, pos, stream=None):
+    """Context on the caller's spacecraft positions pos [rows][3][3] (metres,
+    host array), row j at time t0 + j dt (orbit_kind 2)."""
+    import numpy as np
+    arr = np.ascontiguousarray(pos, dtype=np.float64)
+    if arr.ndim != 3 or arr.shape[1:] != (3, 3):
+        raise ValueError(f"orbit table: shape {arr.shape}, expected (rows, 3, 3)")
+    tab = OrbitTable(float(t0), float(dt), int(arr.shape[0]), arr.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(lib().lisa_td_create_orbits(ctypes.byref(h), ctypes.byref(cfg), ctypes.byref(tab),
+                                       _stream(stream)), "lisa_td_create_orbits")
     return h
 
 
@@ -206,6 +231,13 @@ def lisa_td_residual_loglike_noalloc(cfg, r, W, logl, stream=None):
     _check(lib().lisa_td_residual_loglike_noalloc(ctypes.byref(cfg), _ptr(r), int(W), _ptr(logl),
                                                   _stream(stream)),
            "lisa_td_residual_loglike_noalloc")
+
+
+def lisa_td_fp32_fma_rate(stream=None):
+    """-> the device's FP32 FMA rate in TFLOP/s (measured on the stream)."""
+    v = ctypes.c_double()
+    _check(lib().lisa_td_fp32_fma_rate(ctypes.byref(v), _stream(stream)), "lisa_td_fp32_fma_rate")
+    return v.value
 
 
 def _host_i32(a):
@@ -285,6 +317,10 @@ def flow_create(dim, layers, hidden, max_batch, idx, perms, stream=None):
     return h
 
 
+def flow_set_wait_limit(f, polls):
+    _check(lib().flow_set_wait_limit(f, int(polls)), "flow_set_wait_limit")
+
+
 def flow_nparams(f):
     n = ctypes.c_int64()
     _check(lib().flow_nparams(f, ctypes.byref(n)), "flow_nparams")
@@ -351,11 +387,15 @@ def _need(t, dtype, shape, what):
 class Likelihood:
     """Owns one context; tensors in, tensors out (torch on cuda)."""
 
-    def __init__(self, precision=0, max_walkers=32, stream=None, **cfg):
+    def __init__(self, precision=0, max_walkers=32, stream=None, orbit_table=None, **cfg):
+        """orbit_table: (t0, dt, positions [rows][3][3] in metres) for orbit=2."""
         import torch
         self.torch = torch
         self.cfg = make_config(precision=precision, max_walkers=max_walkers, **cfg)
-        self.ctx = lisa_td_create(self.cfg, stream)
+        if orbit_table is not None:
+            self.ctx = lisa_td_create_orbits(self.cfg, *orbit_table, stream=stream)
+        else:
+            self.ctx = lisa_td_create(self.cfg, stream)
         self.dtype = torch.float64 if precision == 0 else torch.float32
 
     def close(self):

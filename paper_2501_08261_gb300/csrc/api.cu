@@ -44,7 +44,7 @@ void free_ctx(lisa_td_ctx* c) {
   void* ptrs[] = {c->orb64, c->orb32, c->psdw, c->plan.tw_n, c->plan.tw1, c->plan.tw2,
                   c->tdi_tab, c->chan_list, c->data64, c->data32, c->walkers, c->h, c->y,
                   c->r, c->fy, c->partial, c->status, c->tdi_tiles, c->tdi_pairs,
-                  c->tdi_flag};
+                  c->tdi_flag, c->orb_table};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -60,7 +60,7 @@ int check_cfg(const lisa_td_config* g) {
   int p = g->lagrange_order;
   if (!(p == 1 || p == 3 || p == 5 || p == 7 || p == 15 || p == 31))
     return fail(LISA_TD_EINVAL, "lagrange_order must be one of 1, 3, 5, 7, 15, 31");
-  if (g->orbit_kind != 0 && g->orbit_kind != 1) return fail(LISA_TD_EINVAL, "orbit_kind must be 0 or 1");
+  if (g->orbit_kind < 0 || g->orbit_kind > 2) return fail(LISA_TD_EINVAL, "orbit_kind must be 0, 1 or 2");
   if (g->mode_mask < 1 || g->mode_mask > 31) return fail(LISA_TD_EINVAL, "mode_mask must be in 1..31");
   if (g->precessing != 0 && g->precessing != 1) return fail(LISA_TD_EINVAL, "precessing must be 0 or 1");
   if (g->precision != 0 && g->precision != 1) return fail(LISA_TD_EINVAL, "precision must be 0 or 1");
@@ -76,6 +76,61 @@ int check_w(const lisa_td_ctx* c, int W) {
 }
 
 inline int pad32(int w) { return (w + 31) / 32 * 32; }
+
+// The caller's orbit table (orbit_kind 2): coverage of the grid, finite
+// positions, arms near the nominal 2.5e9 m (the TDI and projection halos are
+// sized for them), and the guiding centre's phase and largest offset.
+int check_orbit_table(const lisa_td_config* g, const lisa_td_orbit_table* T, double* phase,
+                      double* dev) {
+  if (!T || !T->pos_host) return fail(LISA_TD_EINVAL, "orbit table is NULL");
+  if (T->rows < 8) return fail(LISA_TD_EINVAL, "orbit table needs at least 8 rows");
+  if (!(T->dt > 0.0) || !isfinite(T->dt) || !isfinite(T->t0))
+    return fail(LISA_TD_EINVAL, "orbit table: t0 must be finite and dt finite and > 0");
+  const double last = g->t0 + (double)(g->n - 1) * g->dt;
+  if (T->t0 > g->t0 - 120.0 || T->t0 + (double)(T->rows - 1) * T->dt < last)
+    return fail(LISA_TD_EINVAL,
+                "orbit table covers [%.6g, %.6g] s; it must start 120 s before the grid "
+                "(%.6g s) and reach its last sample (%.6g s)", T->t0,
+                T->t0 + (double)(T->rows - 1) * T->dt, g->t0, last);
+  const double arm = 2.5e9;
+  const double omega = lisa::kOmegaOrb;            // the guiding centre's rate
+  const double au = lisa::kAUSec * lisa::kC;
+  const int64_t mid = T->rows / 2;
+  double bx = 0.0, by = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    bx += T->pos_host[(mid * 3 + k) * 3 + 0] / 3.0;
+    by += T->pos_host[(mid * 3 + k) * 3 + 1] / 3.0;
+  }
+  *phase = atan2(by, bx) - omega * (T->t0 + (double)mid * T->dt);
+  double worst = 0.0;
+  for (int64_t j = 0; j < T->rows; ++j) {
+    const double* r = T->pos_host + j * 9;
+    for (int q = 0; q < 9; ++q)
+      if (!isfinite(r[q])) return fail(LISA_TD_EINVAL, "orbit table row %lld is not finite", (long long)j);
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3;
+      const double dx = r[a * 3] - r[b * 3], dy = r[a * 3 + 1] - r[b * 3 + 1], dz = r[a * 3 + 2] - r[b * 3 + 2];
+      const double len = sqrt(dx * dx + dy * dy + dz * dz);
+      if (!(len >= 0.9 * arm && len <= 1.08 * arm))
+        return fail(LISA_TD_EINVAL, "orbit table row %lld: arm %d-%d is %.6g m, outside [0.9, 1.08] x 2.5e9 m",
+                    (long long)j, a + 1, b + 1, len);
+    }
+    const double a = omega * (T->t0 + (double)j * T->dt) + *phase;
+    double off2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double gd = d == 0 ? au * cos(a) : (d == 1 ? au * sin(a) : 0.0);
+      const double bd = (r[d] + r[3 + d] + r[6 + d]) / 3.0 - gd;
+      off2 += bd * bd;
+    }
+    worst = fmax(worst, sqrt(off2));
+  }
+  *dev = worst / lisa::kC;
+  if (g->precision == 1 && worst > 0.1 * au)
+    return fail(LISA_TD_ERANGE,
+                "orbit table: the constellation's barycentre leaves the 1 AU guiding circle by "
+                "%.3g AU (the mixed path allows 0.1 AU)", worst / au);
+  return LISA_TD_OK;
+}
 
 }  // namespace
 
@@ -115,17 +170,47 @@ extern "C" {
 
 const char* lisa_td_last_error(void) { return g_err; }
 
-int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
+static int create_ctx(lisa_td_ctx** out, const lisa_td_config* cfg,
+                      const lisa_td_orbit_table* orbits, void* stream) {
   g_err[0] = 0;
   if (!out) return fail(LISA_TD_EINVAL, "out is NULL");
   *out = nullptr;
   if (!cfg) return fail(LISA_TD_EINVAL, "cfg is NULL");
   int rc = check_cfg(cfg);
   if (rc) return rc;
+  if (cfg->orbit_kind == 2 && !orbits)
+    return fail(LISA_TD_EINVAL, "orbit_kind 2 takes the caller's table: use lisa_td_create_orbits");
+  if (cfg->orbit_kind != 2 && orbits)
+    return fail(LISA_TD_EINVAL, "an orbit table needs orbit_kind 2");
+  double phase = 0.0, dev = 0.0;
+  if (orbits && (rc = check_orbit_table(cfg, orbits, &phase, &dev)) != 0) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   lisa_td_ctx* c = (lisa_td_ctx*)calloc(1, sizeof(lisa_td_ctx));
   if (!c) return fail(LISA_TD_ENOMEM, "host allocation failed");
   c->cfg = *cfg;
+  c->orb_phase = phase;
+  c->orb_dev = dev;
+  if (orbits) {
+    c->orb_rows = orbits->rows;
+    c->orb_t0 = orbits->t0;
+    c->orb_dt = orbits->dt;
+    const size_t bytes = sizeof(double) * 9 * (size_t)orbits->rows;
+    double* host = (double*)malloc(bytes);
+    if (!host) {
+      free_ctx(c);
+      return fail(LISA_TD_ENOMEM, "host allocation failed");
+    }
+    for (size_t q = 0; q < 9 * (size_t)orbits->rows; ++q) host[q] = orbits->pos_host[q] / lisa::kC;
+    cudaError_t e = cudaMalloc((void**)&c->orb_table, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(c->orb_table, host, bytes, cudaMemcpyHostToDevice);
+    free(host);
+    if (e != cudaSuccess) {
+      if (e == cudaErrorMemoryAllocation) c->orb_table = nullptr;
+      free_ctx(c);
+      cudaGetLastError();
+      return cuda_fail(e, "lisa_td_create_orbits: orbit table");
+    }
+  }
   c->n = cfg->n;
   c->wmax_pad = pad32(cfg->max_walkers);
   c->esize = cfg->precision == 0 ? 8 : 4;
@@ -158,8 +243,14 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
       {(void**)&c->tdi_pairs, sizeof(lisa::TdiTilePair) * ((n + lisa::kTdiTile - 1) / lisa::kTdiTile) * lisa::kTdiPairs},
       {(void**)&c->tdi_flag, sizeof(int)},
   };
+  // host-side fault injection: LISA_TD_FAIL_ALLOC=k makes the k-th workspace
+  // allocation (0-based) fail as if the device were out of memory, so that the
+  // clean-up path and the LISA_TD_ENOMEM report can be tested without a fault
+  const char* inject = getenv("LISA_TD_FAIL_ALLOC");
+  const long fail_at = inject ? strtol(inject, nullptr, 10) : -1;
+  long at = 0;
   for (auto& a : allocs) {
-    cudaError_t e = cudaMalloc(a.p, a.bytes);
+    cudaError_t e = at++ == fail_at ? cudaErrorMemoryAllocation : cudaMalloc(a.p, a.bytes);
     if (e != cudaSuccess) {
       *a.p = nullptr;
       free_ctx(c);
@@ -193,8 +284,31 @@ int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
   // the combined-FIR TDI kernel runs when every pair fits (grids of a few
   // seconds' spacing); finer grids keep one FIR per term
   c->tdi_comb = wide ? 0 : 1;
+  if (c->orb_table) {                              // only the orbit tables read it
+    cudaFree(c->orb_table);
+    c->orb_table = nullptr;
+  }
   *out = c;
   return LISA_TD_OK;
+}
+
+int lisa_td_create(lisa_td_ctx** out, const lisa_td_config* cfg, void* stream) {
+  return create_ctx(out, cfg, nullptr, stream);
+}
+
+int lisa_td_create_orbits(lisa_td_ctx** out, const lisa_td_config* cfg,
+                          const lisa_td_orbit_table* orbits, void* stream) {
+  if (!orbits) {
+    g_err[0] = 0;
+    if (out) *out = nullptr;
+    return fail(LISA_TD_EINVAL, "orbit table is NULL");
+  }
+  if (cfg && cfg->orbit_kind != 2) {
+    g_err[0] = 0;
+    if (out) *out = nullptr;
+    return fail(LISA_TD_EINVAL, "lisa_td_create_orbits needs orbit_kind 2");
+  }
+  return create_ctx(out, cfg, orbits, stream);
 }
 
 int lisa_td_set_data(lisa_td_ctx* c, const double* aet_dev, void* stream) {

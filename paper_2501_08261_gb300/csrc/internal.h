@@ -29,6 +29,14 @@ struct lisa_td_ctx {
   int esize;                       // 8 (FP64) or 4 (mixed)
   lisa::OrbitRec64* orb64;
   lisa::OrbitRec32* orb32;
+  // orbit_kind 2: the caller's positions [rows][3][3] in light-seconds on the
+  // device, their time grid, and the phase of the guiding centre
+  // g(t) = AU (cos(Omega t + orb_phase), sin(Omega t + orb_phase), 0)
+  double* orb_table;
+  int64_t orb_rows;
+  double orb_t0, orb_dt;
+  double orb_phase;                // 0 for the built-in models
+  double orb_dev;                  // largest |barycentre - g(t)| of the table [light-s]
   double* psdw;                    // [2][n/2+1]: dt^2 * 4 df / S (AE, T) in band, else 0,
                                    // followed by the same as float x 2^-160 (psd_bytes)
   lisa::FftPlan plan;

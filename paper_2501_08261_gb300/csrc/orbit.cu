@@ -46,34 +46,68 @@ __device__ void kepler_pos(int craft, double t, double* r) {
   r[2] = zt;
 }
 
-__device__ void craft_pos(int kind, int craft, double t, double* r) {
-  if (kind == 0) rigid_pos(craft, t, r);
-  else kepler_pos(craft, t, r);
+// The caller's table (positions [rows][3][3] in light-seconds, row j at
+// T0 + j Tdt): centred 8-point Lagrange interpolation in the row index, nodes
+// j - 3 .. j + 4 around j = floor((t - T0) / Tdt), the stencil shifted inwards
+// at the table's ends.
+struct OrbitTableView {
+  const double* pos;
+  int64_t rows;
+  double t0, dt;
+};
+
+__device__ void table_pos(const OrbitTableView& T, int craft, double t, double* r) {
+  const double x = (t - T.t0) / T.dt;
+  int64_t j = (int64_t)floor(x);
+  int64_t b = j - 3;
+  b = b < 0 ? 0 : (b > T.rows - 8 ? T.rows - 8 : b);
+  const double u = x - (double)b;                  // position in node units, nodes 0..7
+  double w[8];
+  for (int k = 0; k < 8; ++k) {
+    double num = 1.0, den = 1.0;
+    for (int m = 0; m < 8; ++m) {
+      if (m == k) continue;
+      num *= u - (double)m;
+      den *= (double)(k - m);
+    }
+    w[k] = num / den;
+  }
+  for (int d = 0; d < 3; ++d) {
+    double acc = 0.0;
+    for (int k = 0; k < 8; ++k) acc += w[k] * T.pos[((b + k) * 3 + craft) * 3 + d];
+    r[d] = acc;
+  }
 }
 
-__global__ void orbit_kernel(int64_t n, double t0, double dt, int kind, OrbitRec64* o64,
-                             OrbitRec32* o32) {
+__device__ void craft_pos(int kind, const OrbitTableView& T, int craft, double t, double* r) {
+  if (kind == 0) rigid_pos(craft, t, r);
+  else if (kind == 1) kepler_pos(craft, t, r);
+  else table_pos(T, craft, t, r);
+}
+
+__global__ void orbit_kernel(int64_t n, double t0, double dt, int kind, OrbitTableView T,
+                             double phase, OrbitRec64* o64, OrbitRec32* o32) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double t = t0 + (double)i * dt;
   OrbitRec64 R;
-  for (int k = 0; k < 3; ++k) craft_pos(kind, k, t, R.rr[k]);
+  for (int k = 0; k < 3; ++k) craft_pos(kind, T, k, t, R.rr[k]);
   for (int j = 0; j < kNLink; ++j) {
     int sidx = link_sender(j), ridx = link_receiver(j);
     double L, rs[3];
     if (kind == 0) {
       L = kArmSec;
     } else {                                      // light-time fixed point
-      craft_pos(kind, sidx, t, rs);
+      craft_pos(kind, T, sidx, t, rs);
       double d0 = R.rr[ridx][0] - rs[0], d1 = R.rr[ridx][1] - rs[1], d2 = R.rr[ridx][2] - rs[2];
       L = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
       for (int it = 0; it < 8; ++it) {
-        craft_pos(kind, sidx, t - L, rs);
+        craft_pos(kind, T, sidx, t - L, rs);
         d0 = R.rr[ridx][0] - rs[0]; d1 = R.rr[ridx][1] - rs[1]; d2 = R.rr[ridx][2] - rs[2];
         L = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
       }
     }
-    craft_pos(kind, sidx, t - L, rs);
+    craft_pos(kind, T, sidx, t - L, rs);
     double d[3] = {R.rr[ridx][0] - rs[0], R.rr[ridx][1] - rs[1], R.rr[ridx][2] - rs[2]};
     double nn = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
     for (int q = 0; q < 3; ++q) {
@@ -83,8 +117,9 @@ __global__ void orbit_kernel(int64_t n, double t0, double dt, int kind, OrbitRec
     R.L[j] = L;
   }
   o64[i] = R;
-  // FP32 copy relative to the guiding centre g(t) = AU (cos Omega t, sin Omega t, 0)
-  double a = kOmegaOrb * t;
+  // FP32 copy relative to the guiding centre g(t) = AU (cos(Omega t + phase),
+  // sin(Omega t + phase), 0)
+  double a = kOmegaOrb * t + phase;
   double g[3] = {kAUSec * cos(a), kAUSec * sin(a), 0.0};
   OrbitRec32 F;
   for (int k = 0; k < 3; ++k)
@@ -159,8 +194,9 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 }  // namespace
 
 cudaError_t launch_orbit_tables(const lisa_td_ctx* c, cudaStream_t s) {
-  orbit_kernel<<<nblk(c->n, 128), 128, 0, s>>>(c->n, c->cfg.t0, c->cfg.dt, c->cfg.orbit_kind,
-                                                c->orb64, c->orb32);
+  OrbitTableView T{c->orb_table, c->orb_rows, c->orb_t0, c->orb_dt};
+  orbit_kernel<<<nblk(c->n, 128), 128, 0, s>>>(c->n, c->cfg.t0, c->cfg.dt, c->cfg.orbit_kind, T,
+                                                c->orb_phase, c->orb64, c->orb32);
   return cudaGetLastError();
 }
 

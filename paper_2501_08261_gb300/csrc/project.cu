@@ -32,7 +32,7 @@ template <int K>
 __global__ void __launch_bounds__(128) project_fp64_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec64* __restrict__ orb, const double2* __restrict__ h, double* __restrict__ y,
-    int tile, int halo, const int64_t* __restrict__ woff) {
+    int tile, int halo, const int64_t* __restrict__ woff, double phase) {
   extern __shared__ double2 win[];      // [(tile + 2 halo)][kPW]
   __shared__ int shift_s[32];
   __shared__ double cinv_s[K];
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(128) project_fp64_kernel(
   if (warp == 0) {
     const WalkerRec& R = walkers[w];
     double tc = t0 + ((double)i0 + 0.5 * tile) * dt;
-    double a = kOmegaOrb * tc;
+    double a = kOmegaOrb * tc + phase;
     double S = kAUSec * (R.k[0] * cos(a) + R.k[1] * sin(a));
     shift_s[lane] = (int)floor(S / dt);
   }
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, 2) project_mixed_kernel(
     const WalkerRec* __restrict__ walkers, int W, int ldw, int64_t n, double t0, double dt,
     const OrbitRec32* __restrict__ orb, const float2* __restrict__ h, float* __restrict__ y,
     int tile, int halo, int nL, float rL, const int64_t* __restrict__ woff,
-    const LagrangePairs pairs) {
+    const LagrangePairs pairs, double phase) {
   // shared memory: (h+, hx) pairs [rows][32] -- 256-byte rows, so that a
   // 64-bit load of lane w touches banks 2w, 2w+1 whatever row each walker's
   // stencil is on (conflict-free per half-warp) -- then the orbit records
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256, 2) project_mixed_kernel(
   if (warp == 0) {
     const WalkerRec& R = walkers[w];
     double ta = t0 + (double)i0 * dt;
-    double a = kOmegaOrb * ta;
+    double a = kOmegaOrb * ta + phase;
     double ca = cos(a), sa = sin(a);
     double S = kAUSec * (R.k[0] * ca + R.k[1] * sa);
     double sh = floor(S / dt);
@@ -323,8 +323,11 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
                      cudaStream_t s) {
   const double dt = c->cfg.dt;
   const int tile = c->tune_tile > 0 ? c->tune_tile : 128;
+  // stencils reach k.(r - g) + L + the drift of k.g over the tile from the
+  // guiding centre's shift; orb_dev widens it for the caller's orbit tables
   int halo = (K / 2) + 2 +
-             (int)ceil((1.1 * kArmSec + kArmSec + kAUSec * kOmegaOrb * tile * dt) / dt);
+             (int)ceil((1.1 * kArmSec + kArmSec + c->orb_dev +
+                        kAUSec * kOmegaOrb * tile * dt) / dt);
   int groups = (W + 31) / 32;
   dim3 grid((unsigned)((c->n + tile - 1) / tile), (unsigned)groups);
   dim3 block(32, 4);
@@ -335,7 +338,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
                          (int)smem);
     project_fp64_kernel<K><<<grid, block, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                      c->orb64, (const double2*)h, (double*)y,
-                                                     tile, halo, c->woff);
+                                                     tile, halo, c->woff, c->orb_phase);
   } else {
     size_t smem = (size_t)(tile + 2 * halo) * 32 * sizeof(float2) +
                   (size_t)tile * sizeof(OrbitRec32);
@@ -349,7 +352,7 @@ cudaError_t launch_k(const lisa_td_ctx* c, int W, int ldw, const void* h, void* 
     project_mixed_kernel<K><<<grid, blockm, smem, s>>>(c->walkers, W, ldw, c->n, c->cfg.t0, dt,
                                                       c->orb32, (const float2*)h, (float*)y,
                                                       tile, halo, nL, rL, c->woff,
-                                                      lagrange_pairs<K>());
+                                                      lagrange_pairs<K>(), c->orb_phase);
   }
   return cudaGetLastError();
 }

@@ -121,24 +121,54 @@ def newtonian_time_to_merger(m1, m2, f):
     return 5.0 / 256.0 * (math.pi * f) ** (-8.0 / 3.0) * mc ** (-5.0 / 3.0)
 
 
-def ragged_walkers(w, n, dt, seed, precessing=True, f_min=1e-4, pad_s=2 * DAY):
+def ragged_walkers(w, n, dt, seed, precessing=True, f_min=1e-4, pad_s=0.25 * DAY):
     """Walkers of uneven signal length on an n-sample grid: prior draws whose
-    window T_w = clamp(time to merger from f_min + pad, 1 d, n dt) is rounded up
-    to a whole number of days k with k in RAGGED_DAYS; the merger sits at
-    t_c = t_end - U(0.02, 0.10) T_w inside the window.  -> (params, n_w)."""
+    window T_w (the stretch of data up to shortly after the merger) is drawn
+    log-uniformly between 1 day and the grid length, shortened to the time to
+    merger from f_min plus a ringdown pad where the signal is shorter, and
+    rounded to the nearest whole number of days k with k in RAGGED_DAYS; the merger
+    sits at t_c = t_end - U(0.02, 0.10) T_w inside the window.  -> (params, n_w)."""
     rng = np.random.default_rng(seed + 7)
     th = prior_draws(w, n, dt, seed, precessing=precessing)
     days_max = n * dt / DAY
     nw = np.empty(w, dtype=np.int64)
     for k in range(w):
         tau = newtonian_time_to_merger(th[k, 0], th[k, 1], f_min) + pad_s
-        d = min(max(tau / DAY, 1.0), days_max)
-        kd = next((q for q in RAGGED_DAYS if q >= d - 1e-9 and q <= days_max), None)
-        if kd is None:
-            kd = max(q for q in RAGGED_DAYS if q <= days_max)
+        want = days_max ** rng.uniform(0.0, 1.0)         # log-uniform in [1, days_max] d
+        d = min(max(min(want, tau / DAY), 1.0), days_max)
+        kd = min((q for q in RAGGED_DAYS if q <= days_max), key=lambda q: abs(q - d))
         nw[k] = int(round(kd * DAY / dt))
         th[k, 14] = n * dt - rng.uniform(0.02, 0.10) * nw[k] * dt
     return th, nw
+
+
+def orbit_table_positions(t_start, dt_table, rows, seed, phase=-20.0 * math.pi / 180.0):
+    """A synthetic mission orbit file: the three spacecraft's positions [m]
+    at times t_start + j dt_table, shape [rows][3][3].  Each spacecraft
+    follows the first-order eccentric-orbit (cartwheel) expansion about a
+    1 AU circle at the sidereal rate, the constellation trailing by `phase`,
+    with arms near 2.5e9 m, plus a seeded small radial breathing (1e-4 AU,
+    twice a year) that makes the arms flex differently from the built-in
+    models.  An input recipe: the library and the oracle resample it."""
+    rng = np.random.default_rng(seed)
+    au, arm = 149597870700.0, 2.5e9
+    omega = 2.0 * math.pi / (365.25636 * DAY)
+    e = arm / (2.0 * math.sqrt(3.0) * au)
+    t = t_start + dt_table * np.arange(rows)
+    a = omega * t + phase
+    out = np.zeros((rows, 3, 3))
+    for k in range(3):
+        b = 2.0 * math.pi * k / 3.0 + phase
+        x = au * np.cos(a) + au * e * (np.sin(a) * np.cos(a) * np.sin(b)
+                                       - (1.0 + np.sin(a) ** 2) * np.cos(b))
+        y = au * np.sin(a) + au * e * (np.sin(a) * np.cos(a) * np.cos(b)
+                                       - (1.0 + np.cos(a) ** 2) * np.sin(b))
+        z = -math.sqrt(3.0) * au * e * np.cos(a - b)
+        breath = 1.0 + 1e-4 * np.sin(2.0 * omega * t + rng.uniform(0.0, 2.0 * math.pi))
+        out[:, k, 0] = x * breath
+        out[:, k, 1] = y * breath
+        out[:, k, 2] = z
+    return out
 
 
 def table1_precessing(n, dt, tc_frac=0.9):

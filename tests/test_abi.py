@@ -82,3 +82,47 @@ def test_flow_and_sampler_argument_errors_need_no_gpu(libpath):
     assert lib.flow_create(ctypes.byref(h), 15, 1, 128, 64, bad, perm, None) == -1
     assert lib.lisa_fisher_npoints(15) == 451
     assert lib.lisa_cholesky(None, None, 3, None, None, None) == -1
+
+
+def test_orbit_table_checks_need_no_gpu(libpath):
+    """lisa_td_create_orbits validates the table on the host before any CUDA
+    call: NULL, too few rows, a grid not covered, non-physical arms."""
+    import numpy as np
+    from paper_2501_08261_gb300 import workloads
+    lib = api.load_library(libpath)
+    cfg = api.make_config(dt=5.0, n=17280, orbit=2, tdi_gen=20)
+    h = ctypes.c_void_p()
+    assert lib.lisa_td_create_orbits(ctypes.byref(h), ctypes.byref(cfg), None, None) == -1
+    good = workloads.orbit_table_positions(-7200.0, 3600.0, 40, 3)
+
+    def call(t0, dt, pos, c=cfg):
+        arr = np.ascontiguousarray(pos)
+        tab = api.OrbitTable(t0, dt, arr.shape[0], arr.ctypes.data)
+        return lib.lisa_td_create_orbits(ctypes.byref(h), ctypes.byref(c), ctypes.byref(tab), None)
+    assert call(-7200.0, 3600.0, good[:7]) == -1                      # rows < 8
+    assert b"8 rows" in lib.lisa_td_last_error()
+    assert call(-60.0, 3600.0, good) == -1                            # starts too late
+    assert call(-7200.0, 3600.0, good[:20]) == -1                     # ends before the grid
+    assert b"cover" in lib.lisa_td_last_error()
+    bad = good.copy()
+    bad[5, 1] *= 1.01                                                 # a craft 0.01 AU off
+    assert call(-7200.0, 3600.0, bad) == -1
+    assert b"arm" in lib.lisa_td_last_error()
+    nan = good.copy()
+    nan[3, 2, 1] = float("nan")
+    assert call(-7200.0, 3600.0, nan) == -1
+    kind1 = api.make_config(dt=5.0, n=17280, orbit=1)
+    assert call(-7200.0, 3600.0, good, kind1) == -1                   # needs orbit_kind 2
+    assert lib.lisa_td_create(ctypes.byref(h), ctypes.byref(cfg), None) == -1
+
+
+def test_allocation_failure_injection_needs_no_gpu(libpath, monkeypatch):
+    """LISA_TD_FAIL_ALLOC=0 fails the first workspace allocation before any
+    CUDA call: LISA_TD_ENOMEM and a NULL context."""
+    lib = api.load_library(libpath)
+    cfg = api.make_config(dt=5.0, n=17280)
+    h = ctypes.c_void_p(1)
+    monkeypatch.setenv("LISA_TD_FAIL_ALLOC", "0")
+    assert lib.lisa_td_create(ctypes.byref(h), ctypes.byref(cfg), None) == -2
+    assert h.value is None
+    assert b"cudaMalloc" in lib.lisa_td_last_error()

@@ -155,3 +155,52 @@ def test_band_limits():
     assert not m[0] and not m[-1]
     assert np.all(f[m] >= 1e-4) and np.all(f[m] <= 0.02)
     assert m.sum() == np.sum((f >= 1e-4) & (f <= 0.02))
+
+
+# ------------------------------------------------------ orbit tables --------
+def test_orbit_table_interpolation_is_exact_for_degree_seven_paths():
+    """The table's resampling is the degree-7 Lagrange polynomial through eight
+    rows: it reproduces trajectories that are polynomials of degree <= 7 in
+    time to rounding (near the ends too, where the eight rows move inwards),
+    and no longer does at degree 8."""
+    rng = np.random.default_rng(11)
+    t0, dt, rows = -7200.0, 3600.0, 40
+    tt = t0 + dt * np.arange(rows)
+    ts = np.concatenate([rng.uniform(t0, tt[-1], 200), [t0, t0 + 0.3 * dt, tt[-1] - 0.2 * dt]])
+    c = rng.normal(size=(8, 3, 3)) * 1e9
+
+    def path(t):
+        x = (np.asarray(t) - t0) / (rows * dt)
+        return sum(c[d] * x[..., None, None] ** d for d in range(8))
+    tab = orbits.OrbitTable(t0, dt, path(tt))
+    for k in (1, 2, 3):
+        want = path(ts)[:, k - 1, :] / K.C_SI
+        err = np.max(np.abs(tab.position(k, ts) - want)) / np.max(np.abs(want))
+        assert err < 1e-12, (k, err)
+    # x^8 on one stencil's rows: the error at the middle is prod (3.5 - k) = 43
+    # against a largest value of 7^8
+    p8 = np.zeros((8, 3, 3))
+    p8[:, 0, 0] = np.arange(8.0) ** 8
+    got = orbits.OrbitTable(0.0, dt, p8).position(1, np.array([3.5 * dt]))[0, 0] * K.C_SI
+    assert abs(got - 3.5 ** 8) == pytest.approx(43.06640625, rel=1e-9)
+
+
+def test_orbit_table_of_keplerian_positions_reproduces_the_keplerian_model():
+    """Keplerian positions tabulated hourly and resampled through the table:
+    positions, light times and A, E, T of a source agree with the analytic
+    Keplerian model to the interpolant's error (Omega dt ~ 7e-4 rad per row)."""
+    t0, dt = -3 * 3600.0, 3600.0
+    rows = 12
+    tt = t0 + dt * np.arange(rows)
+    pos = np.stack([orbits.kepler_position(k, tt) for k in (1, 2, 3)], axis=1) * K.C_SI
+    tab = orbits.OrbitTable(t0, dt, pos)
+    ts = np.linspace(0.0, 4 * 3600.0, 77)
+    for k in (1, 2, 3):
+        assert np.max(np.abs(tab.position(k, ts) - orbits.kepler_position(k, ts))) < 1e-9
+    for l in orbits.LINKS:
+        assert np.max(np.abs(orbits.light_time(tab, l, ts) - orbits.light_time("kepler", l, ts))) < 1e-11
+    th = np.array([6e5, 3e5, 0.4, 0, 0, -0.2, 0, 0, 3.0, 0.7, 1.1, 0.3, 2.0, 0.4, 2.5 * 3600.0])
+    sk = pipeline.Setup(n=2880, tdi_gen=20, orbit="kepler", mode_mask=31)
+    st = pipeline.Setup(n=2880, tdi_gen=20, orbit=tab, mode_mask=31)
+    a, b = pipeline.aet(th, sk), pipeline.aet(th, st)
+    assert np.max(np.abs(a - b)) <= 1e-9 * np.max(np.abs(a))
