@@ -14,6 +14,8 @@ flow learns from, and the trained flow is the learned independence proposal.
 ``ess`` is the effective sample size from the integrated autocorrelation
 time with Sokal's automatic window (analysis of recorded chains, host side).
 """
+import math
+
 import numpy as np
 
 from . import api
@@ -133,6 +135,48 @@ class PT(MH):
         self.swap()
         return acc
 
+    def _slices(self):
+        W = self.Wt
+        return [slice(k * W, (k + 1) * W) for k in range(self.T)]
+
+    def set_flow_logq(self, flows):
+        """log q of every walker's state under its own temperature's flow (the
+        state moves between temperatures at each exchange, so this is redone
+        before every flow step)."""
+        for sl, f in zip(self._slices(), flows):
+            api.flow_logprob(f, self.x[sl], self.Wt, self.logq[sl])
+
+    def step_flows(self, flows, D):
+        """Independence proposals from a flow per temperature (flows[k] trained
+        on temperature k's chain), the tempered MH decision on the exact
+        likelihood, then replica exchange."""
+        torch = self.torch
+        self.set_flow_logq(flows)
+        z = torch.randn((self.W, D), generator=self.gen, dtype=torch.float64, device="cuda")
+        for sl, f in zip(self._slices(), flows):
+            api.flow_propose(f, z[sl], self.Wt, self.xp[sl], self.logqp[sl])
+        acc = self._accept(self.lik.loglike(self.xp)).clone()
+        self.swap()
+        return acc
+
+    def set_gauss_logq(self, mus, Ls, idx):
+        for sl, mu, L in zip(self._slices(), mus, Ls):
+            api.lisa_gauss_logq(mu, L, idx, self.x[sl], self.Wt, self.logq[sl])
+
+    def step_gauss_tempered(self, mus, Ls, idx):
+        """Independence proposals N(mu_k, (L_k L_k^T)^-1) per temperature
+        (the Fisher-Gaussian widened to the tempered posterior), the tempered
+        MH decision, then replica exchange."""
+        torch = self.torch
+        self.set_gauss_logq(mus, Ls, idx)
+        z = torch.randn((self.W, len(idx)), generator=self.gen, dtype=torch.float64,
+                        device="cuda")
+        for sl, mu, L in zip(self._slices(), mus, Ls):
+            api.lisa_gauss_draw(mu, L, idx, z[sl], self.Wt, self.xp[sl], self.logqp[sl])
+        acc = self._accept(self.lik.loglike(self.xp)).clone()
+        self.swap()
+        return acc
+
     def swap(self):
         torch = self.torch
         u = 1.0 - torch.rand((self.T - 1) * self.Wt, generator=self.gen, dtype=torch.float64,
@@ -160,6 +204,96 @@ def fisher(lik64, theta0, idx, eps):
     F = torch.empty((D, D), dtype=torch.float64, device="cuda")
     api.lisa_fisher_assemble(logl, eps, F)
     return F
+
+
+# parameters an aligned-spin source depends on (the tilts and spin azimuths
+# of the precessing parameterisation do not enter)
+ALIGNED_IDX = [0, 1, 2, 5, 8, 9, 10, 11, 12, 13, 14]
+# finite-difference steps: relative for masses and distance, absolute otherwise
+EPS_REL = {0: 1e-5, 1: 1e-5, 8: 1e-4}
+EPS_ABS = {14: 0.05}
+
+
+def fd_steps(theta):
+    return np.array([EPS_REL[k] * theta[k] if k in EPS_REL else EPS_ABS.get(k, 1e-3)
+                     for k in range(15)])
+
+
+def fisher_diag(lik64, theta0, idx, eps):
+    """The diagonal F_aa alone: the three-point stencil of each parameter
+    (lisa_fisher_points with one index), all evaluated as one batch."""
+    import torch
+    D = len(idx)
+    th = torch.as_tensor(np.asarray(theta0, dtype=np.float64), device="cuda")
+    pts = torch.empty((3 * D, 15), dtype=torch.float64, device="cuda")
+    for q, a in enumerate(idx):
+        api.lisa_fisher_points(th, [a], [float(eps[q])], pts[3 * q:3 * q + 3])
+    logl = lik64.loglike(pts)
+    out = np.empty(D)
+    f = torch.empty((1, 1), dtype=torch.float64, device="cuda")
+    for q in range(D):
+        api.lisa_fisher_assemble(logl[3 * q:3 * q + 3].contiguous(), [float(eps[q])], f)
+        out[q] = float(f.item())
+    return out
+
+
+def fisher_scaled(lik64, theta0, idx, eps0, frac=0.3, passes=4):
+    """The Fisher matrix with steps matched to the data.  Each step becomes
+    frac / sqrt(F_aa), a fraction of the parameter's conditional width where
+    logL is quadratic (kept within [1e-6, 10] x eps0), with F_aa from
+    three-point stencils repeated until the steps settle; then the full
+    stencil.  At high SNR the conditional widths of the masses are far below
+    any fixed relative step, and second differences over such steps are not a
+    Hessian."""
+    idx = list(idx)
+    e0 = np.asarray(eps0, dtype=np.float64)[idx]
+    eps = e0.copy()
+    for _ in range(passes):
+        d = fisher_diag(lik64, theta0, idx, eps)
+        new = np.where(d > 0, frac / np.sqrt(np.where(d > 0, d, 1.0)), eps)
+        new = np.clip(new, 1e-6 * e0, 10.0 * e0)
+        done = np.all(np.abs(np.log(new / eps)) < math.log(1.5))
+        eps = new
+        if done:
+            break
+    return fisher(lik64, theta0, idx, eps)
+
+
+def box_around(theta, tc_halfwidth=600.0):
+    """A broad uniform box around theta (masses and distance within a factor
+    of two, spins within [-0.99, 0.99], angles over their full ranges, the
+    merger time +- tc_halfwidth): the prior widths that regularise the Fisher
+    matrix along directions the data leave unconstrained."""
+    th = np.asarray(theta, dtype=np.float64)
+    lo = np.array([0.5 * th[0], 0.5 * th[1], -0.99, 0.0, -np.pi, -0.99, 0.0, -np.pi,
+                   0.5 * th[8], 0.0, 0.0, -0.5 * np.pi, 0.0, 0.0, th[14] - tc_halfwidth])
+    hi = np.array([2.0 * th[0], 2.0 * th[1], 0.99, np.pi, np.pi, 0.99, np.pi, np.pi,
+                   2.0 * th[8], np.pi, 2.0 * np.pi, 0.5 * np.pi, 2.0 * np.pi, np.pi,
+                   th[14] + tc_halfwidth])
+    return lo, hi
+
+
+def fisher_ball(lik64, theta0, idx, count, seed, lo=None, hi=None):
+    """`count` draws theta ~ N(theta0, (F + diag(12/w^2))^-1) in the parameters
+    idx (the others stay at theta0): the posterior bulk around an injection at
+    theta0, from the FP64 likelihood's Fisher matrix.  -> device [count][15]."""
+    import torch
+    if lo is None:
+        lo, hi = box_around(theta0)
+    F = fisher_scaled(lik64, theta0, idx, fd_steps(np.asarray(theta0, dtype=np.float64)))
+    L = gauss_factor(F, idx, lo, hi)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    D = len(idx)
+    z = torch.randn((count, D), generator=gen, dtype=torch.float64, device="cuda")
+    mu = torch.as_tensor(np.asarray(theta0, dtype=np.float64), device="cuda")
+    x = torch.empty((count, 15), dtype=torch.float64, device="cuda")
+    q = torch.empty(count, dtype=torch.float64, device="cuda")
+    api.lisa_gauss_draw(mu, L, idx, z, count, x, q)
+    # keep the draws inside the box (spins must stay below 1 in magnitude)
+    x = torch.maximum(torch.minimum(x, torch.as_tensor(hi, device="cuda")),
+                      torch.as_tensor(lo, device="cuda"))
+    return x.contiguous()
 
 
 def gauss_factor(F, idx, lo, hi):

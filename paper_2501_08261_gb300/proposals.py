@@ -15,14 +15,7 @@ import numpy as np
 
 from . import api, mcmc, workloads
 
-# finite-difference steps: relative for masses and distance, absolute otherwise
-EPS_REL = {0: 1e-5, 1: 1e-5, 8: 1e-4}
-EPS_ABS = {14: 0.05}
-
-
-def fd_steps(theta):
-    return np.array([EPS_REL[k] * theta[k] if k in EPS_REL else EPS_ABS.get(k, 1e-3)
-                     for k in range(15)])
+fd_steps = mcmc.fd_steps
 
 
 def flow_init(perms, D, L, H, seed):
@@ -111,4 +104,121 @@ def compare(cfg_name="c3_prec_1d", W=512, rw_steps=600, burn=100, steps=600, epo
                  "gpu_ms": ms_f, "ess_per_s": ess_f / (ms_f * 1e-3),
                  "train_ms": train_ms, "train_samples": len(samples), "epochs": epochs,
                  "loss_first_last": [float(lv[0]), float(lv[-1])]},
+    }
+
+
+def _train_flow(samples, idx, layers, epochs, batch, lr, seed, max_batch):
+    """A flow on `samples` [S][15] (host), trained on the tensor cores: -> (flow,
+    training GPU ms)."""
+    import torch
+    D = len(idx)
+    rng = np.random.default_rng(seed)
+    perms = np.stack([rng.permutation(D) for _ in range(layers)])
+    fl = api.flow_create(D, layers, 128, max(max_batch, batch), idx, perms)
+    api.flow_set_params(fl, torch.as_tensor(flow_init(perms, D, layers, 128, seed + 1),
+                                            device="cuda"))
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    api.flow_set_frame(fl, T(samples.mean(axis=0)), T(samples[:, idx].std(axis=0) + 1e-300))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.flow_train(fl, T(samples), len(samples), epochs, batch, lr, None)
+    e1.record()
+    torch.cuda.synchronize()
+    return fl, e0.elapsed_time(e1)
+
+
+def _pt_run(pt, step, steps, record=False):
+    """`steps` tempered steps: -> (acceptance per temperature [T], cold-chain
+    record [steps][W][15] or None, GPU ms)."""
+    import torch
+    T, W = pt.T, pt.Wt
+    acc = torch.zeros(T * W, dtype=torch.float64, device="cuda")
+    cold = torch.empty((steps, W, 15), dtype=torch.float64, device="cuda") if record else None
+    allx = torch.empty((steps, T * W, 15), dtype=torch.float64, device="cuda") if record == "all" else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for it in range(steps):
+        acc += step()
+        if record:
+            cold[it].copy_(pt.x[:W])
+        if allx is not None:
+            allx[it].copy_(pt.x)
+    e1.record()
+    torch.cuda.synchronize()
+    rate = (acc.view(T, W).mean(dim=1) / steps).cpu().numpy()
+    out = allx.cpu().numpy() if allx is not None else (cold.cpu().numpy() if record else None)
+    return rate, out, e0.elapsed_time(e1)
+
+
+def compare_tempered(cfg_name="c3_prec_1d", T=4, W=256, beta_min=1e-3, rw_steps=600, burn=200,
+                     steps=200, epochs=40, batch=4096, lr=1e-3, layers=6, seed=2):
+    """Parallel tempering with a flow per temperature (the ptemcee-like
+    sampler of Sec. II.C with T temperatures): a Fisher random walk at every
+    temperature generates each temperature's training chain, one flow is
+    trained per temperature, and the tempered independence chains of the flows
+    and of the per-temperature Fisher-Gaussians N(theta_inj, F^-1 / beta) run
+    from the same state, every proposal judged by the exact likelihood and
+    replicas exchanged after each step.  Reports acceptance per temperature
+    and the cold chain's effective samples per second."""
+    import torch
+    cfg = workloads.config(cfg_name)
+    kw = {k: cfg[k] for k in ("dt", "n", "t0", "f_lo", "f_hi", "tdi_gen", "channel_mask",
+                              "lagrange_order", "orbit", "mode_mask", "precessing")}
+    truth = workloads.table1_precessing(cfg["n"], cfg["dt"], tc_frac=0.75)
+    idx = list(range(15))
+    D = len(idx)
+    lo, hi = workloads.table1_prior_box(truth[14])
+    Tt = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    lik64 = api.Likelihood(precision=0, max_walkers=api.lisa_fisher_npoints(D), **kw)
+    lik = api.Likelihood(precision=1, max_walkers=T * W, **kw)
+    d = lik64.tdi(lik64.project(Tt(truth[None])))[:, :, 0].contiguous()
+    lik64.set_data(d)
+    lik.set_data(d)
+    F = mcmc.fisher(lik64, truth, idx, fd_steps(truth))
+    L = mcmc.gauss_factor(F, idx, lo, hi)
+    betas = mcmc.geometric_ladder(T, beta_min)
+    pt = mcmc.PT(lik, lo, hi, W, betas, seed=seed)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed + 100)
+    x0 = torch.empty((T * W, 15), dtype=torch.float64, device="cuda")
+    q0 = torch.empty(T * W, dtype=torch.float64, device="cuda")
+    api.lisa_gauss_draw(Tt(truth), L, idx, torch.randn((T * W, D), generator=gen,
+                                                        dtype=torch.float64, device="cuda"),
+                        T * W, x0, q0)
+    x0 = torch.minimum(torch.maximum(x0, Tt(lo)), Tt(hi)).contiguous()
+    pt.start(x0)
+    acc_rw, rw, ms_rw = _pt_run(pt, lambda: pt.step_walk(L, idx, 2.38 / math.sqrt(D)),
+                                rw_steps, record="all")
+    flows, train_ms = [], 0.0
+    for k in range(T):
+        samples = rw[burn:, k * W:(k + 1) * W].reshape(-1, 15)
+        fl, ms = _train_flow(samples, idx, layers, epochs, batch, lr, seed + 10 * k, T * W)
+        flows.append(fl)
+        train_ms += ms
+    start = pt.x.clone()
+    mus = [Tt(truth)] * T
+    Ls = [(L * math.sqrt(b)).contiguous() for b in betas]
+    pt.start(start)
+    acc_g, gc, ms_g = _pt_run(pt, lambda: pt.step_gauss_tempered(mus, Ls, idx), steps,
+                              record=True)
+    ess_g, tau_g = mcmc.ess(gc, idx)
+    pt.start(start)
+    acc_f, fc, ms_f = _pt_run(pt, lambda: pt.step_flows(flows, D), steps, record=True)
+    ess_f, tau_f = mcmc.ess(fc, idx)
+    for fl in flows:
+        api.flow_destroy(fl)
+    lik.close()
+    lik64.close()
+    return {
+        "workload": f"{cfg_name}: Table I precessing injection, {T} temperatures "
+                    f"(geometric ladder to beta = {beta_min:g}) x {W} walkers, {D} parameters",
+        "betas": [float(b) for b in betas],
+        "fisher_random_walk": {"acceptance": [float(a) for a in acc_rw], "steps": rw_steps,
+                               "gpu_ms": ms_rw},
+        "fisher_gauss": {"acceptance": [float(a) for a in acc_g], "steps": steps, "tau": tau_g,
+                         "ess_cold": ess_g, "ess_cold_per_s": ess_g / (ms_g * 1e-3)},
+        "flow": {"acceptance": [float(a) for a in acc_f], "steps": steps, "tau": tau_f,
+                 "ess_cold": ess_f, "ess_cold_per_s": ess_f / (ms_f * 1e-3),
+                 "train_ms": train_ms,
+                 "ess_cold_per_s_amortised": ess_f / ((ms_f + train_ms + ms_rw) * 1e-3)},
     }
