@@ -47,6 +47,16 @@ int flow_create(flow_ctx** out, int32_t dim, int32_t layers, int32_t hidden, int
 
 int flow_nparams(const flow_ctx* f, int64_t* n);
 
+/* Limit of every wait of the flow kernels on their tensor-core work, in
+ * polls of the mbarrier (failure-path testing; no paper counterpart).
+ * polls < 0 restores the default (2^22 polls, far beyond any product's
+ * duration); 0 makes the first wait of each CTA give up at once.  A wait that
+ * gives up marks the context, the CTA stops issuing products, waits (with the
+ * default limit) for the product already in flight, frees its tensor memory
+ * and ends; the next call on the context returns LISA_TD_ETIMEOUT and clears
+ * the mark.  LISA_TD_ERANGE above the default. */
+int flow_set_wait_limit(flow_ctx* f, int64_t polls);
+
 /* Copy packed FP32 parameters in / out (device pointers, [nparams]).
  * flow_set_params also resets the Adam moments and step count. */
 int flow_set_params(flow_ctx* f, const float* params_dev, void* stream);

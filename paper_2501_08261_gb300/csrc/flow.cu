@@ -46,6 +46,7 @@ struct FlowArgs {
   const float* master;           // packed fp32 parameters
   const double* mu;              // [15]
   const double* scale;           // [D]
+  uint32_t wait_polls;           // limit of a wait on tensor-core work (flow_set_wait_limit)
 };
 
 __device__ __forceinline__ float pick(const float (&v)[kMaxD], int k) {
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kRows, 1) flow_fwd_kernel(FlowArgs a, const do
     __syncthreads();
     // GEMM 1: pre1 = u_a W1^T -> TMEM columns 0..127
     if (tid == 0) gemm_issue(tbase, sA1, sW1, 16, kH, &mbar);
-    ok = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    ok = tc::mbar_wait(&mbar, phase, a.wait_polls);
     phase ^= 1;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after();
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kRows, 1) flow_fwd_kernel(FlowArgs a, const do
     __syncthreads();
     // GEMM 2: pre2 = h1 W2^T -> columns 128..255
     if (tid == 0) gemm_issue(tbase + 128, sH, sW2, kH, kH, &mbar);
-    ok = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    ok = tc::mbar_wait(&mbar, phase, a.wait_polls);
     phase ^= 1;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after();
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kRows, 1) flow_fwd_kernel(FlowArgs a, const do
     __syncthreads();
     // GEMM 3: (s_raw, t) = h2 W3^T -> columns 0..15
     if (tid == 0) gemm_issue(tbase, sH, sW3, kH, 16, &mbar);
-    ok = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    ok = tc::mbar_wait(&mbar, phase, a.wait_polls);
     phase ^= 1;
     if (!__syncthreads_and(ok)) { ok = false; break; }
     tc::fence_after();
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kRows, 1) flow_bwd_kernel(FlowArgs a, const fl
   uint32_t phase = 0;
   bool ok = true;
   auto wait_all = [&]() -> bool {
-    bool w = tc::mbar_wait(&mbar, phase, kWaitPolls);
+    bool w = tc::mbar_wait(&mbar, phase, a.wait_polls);
     phase ^= 1;
     w = __syncthreads_and(w);
     tc::fence_after();
@@ -746,6 +747,7 @@ int flow_create(flow_ctx** out, int32_t dim, int32_t layers, int32_t hidden, int
   FlowArgs& a = f->args;
   a.D = dim;
   a.L = layers;
+  a.wait_polls = kWaitPolls;
   for (int k = 0; k < dim; ++k) {
     if (idx_host[k] < 0 || idx_host[k] > 14) { free_flow(f); return flow_err(LISA_TD_EINVAL, "idx entries must be in 0..14"); }
     for (int j = 0; j < k; ++j)
@@ -813,6 +815,13 @@ int flow_create(flow_ctx** out, int32_t dim, int32_t layers, int32_t hidden, int
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { free_flow(f); return cuda_err(e, "flow_create"); }
   *out = f;
+  return LISA_TD_OK;
+}
+
+int flow_set_wait_limit(flow_ctx* f, int64_t polls) {
+  if (!f) return flow_err(LISA_TD_EINVAL, "NULL context");
+  if (polls > (int64_t)kWaitPolls) return flow_err(LISA_TD_ERANGE, "polls above the default limit");
+  f->args.wait_polls = polls < 0 ? kWaitPolls : (uint32_t)polls;
   return LISA_TD_OK;
 }
 
