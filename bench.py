@@ -36,7 +36,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5
 # DRAM bytes (read + write) per walker-sample of each kernel, from one ncu
 # capture of 30 d x 64 walkers; traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
-NCU_BYTES_PER_UNIT = {"tdi": 1228.392704e6 / (518400 * 64),
+NCU_BYTES_PER_UNIT = {"tdi": None,
                       "project": 1216.544000e6 / (518400 * 64)}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -145,33 +145,77 @@ def _time_steps(torch, fn, steps, barrier):
     return e0.elapsed_time(e1)
 
 
+def _oracle_segment_setup(cfg, seg):
+    from oracle import pipeline
+    return pipeline.Setup(dt=cfg["dt"], n=seg, t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
+                          tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
+                          lagrange_order=cfg["lagrange_order"],
+                          orbit={0: "rigid", 1: "kepler"}[cfg["orbit"]],
+                          mode_mask=cfg["mode_mask"], precessing=bool(cfg["precessing"]))
+
+
+def _oracle_worker(job):
+    """One oracle logL on a segment of the workload (run in a spawned process,
+    one thread): -> seconds."""
+    cfg, seg, theta, data = job
+    from oracle import pipeline
+    s = _oracle_segment_setup(cfg, seg)
+    t = time.perf_counter()
+    pipeline.loglike(theta, s, data)
+    return time.perf_counter() - t
+
+
+def _oracle_pool():
+    """A process pool over all host cores, started with spawn (never forked
+    from a process that holds a CUDA context), one thread per process."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    cores = os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(cores), cores
+
+
+def _segment_inputs(cfg, theta, data_np, seg):
+    import numpy as np
+    th = np.array(theta, dtype=np.float64)
+    th[14] = 0.9 * seg * cfg["dt"]
+    return th, np.ascontiguousarray(np.asarray(data_np)[:, :seg])
+
+
 def cpu_baseline(cfg, theta, data_np, seconds_budget=20.0):
     """The FP64 oracle on a bounded sample: one walker on a segment of the
-    workload's grid (same physics), scaled by n to full-length evals/s."""
-    import numpy as np
+    workload's grid (same physics), scaled by n to full-length evals/s; timed
+    on one core and on all host cores (one process per core)."""
     from oracle import pipeline
     seg = min(cfg["n"], 129600)                       # 7.5 days
-    s = pipeline.Setup(dt=cfg["dt"], n=seg, t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
-                       tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
-                       lagrange_order=cfg["lagrange_order"],
-                       orbit={0: "rigid", 1: "kepler"}[cfg["orbit"]],
-                       mode_mask=cfg["mode_mask"], precessing=bool(cfg["precessing"]))
-    th = theta.copy()
-    th[14] = 0.9 * seg * cfg["dt"]
-    d = np.asarray(data_np)[:, :seg]
+    s = _oracle_segment_setup(cfg, seg)
+    th, d = _segment_inputs(cfg, theta, data_np, seg)
     t = time.perf_counter()
     reps = 0
     while True:
         pipeline.loglike(th, s, d)
         reps += 1
-        if time.perf_counter() - t > seconds_budget * 0.5 or reps >= 3:
+        if time.perf_counter() - t > seconds_budget * 0.25 or reps >= 2:
             break
     el = (time.perf_counter() - t) / reps
-    per_eval_full = el * cfg["n"] / seg
-    return {"value": 1.0 / per_eval_full, "unit": "logL evals/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 walker, {seg}-sample ({seg * cfg['dt'] / 86400:.1f} d) segment of the "
-                      f"workload, {reps} evals, {el:.2f} s each, scaled by n to the "
-                      f"{cfg['n']}-sample series"}
+    scale = cfg["n"] / seg
+    single = 1.0 / (el * scale)
+    pool, cores = _oracle_pool()
+    try:
+        pool.map(_oracle_worker, [(cfg, 256, th, d[:, :256])] * cores)   # start-up, imports
+        t = time.perf_counter()
+        pool.map(_oracle_worker, [(cfg, seg, th, d)] * cores, chunksize=1)
+        wall = time.perf_counter() - t
+    finally:
+        pool.close()
+        pool.join()
+    allcore = cores / (wall * scale)
+    return {"value": allcore, "unit": "logL evals/s", "cores": cores, "kind": "oracle",
+            "single_core_value": single,
+            "sample": f"1 walker per core, {seg}-sample ({seg * cfg['dt'] / 86400:.1f} d) segment "
+                      f"of the workload, one eval per core in {wall:.2f} s wall on {cores} "
+                      f"processes (single core: {reps} evals, {el:.2f} s each), scaled by n to "
+                      f"the {cfg['n']}-sample series"}
 
 
 def _inject(torch, api, lk_ref, lk_all, params, n, snr=2000.0):
@@ -294,6 +338,20 @@ def run_ours(args):
     lk64 = None if args.skip_fp64 else api.Likelihood(precision=0, max_walkers=W, **kw)
     aet, rho0 = _inject(torch, api, lk64 or lk32, [lk for lk in (lk32, lk64) if lk], params,
                         cfg["n"])
+    nball, ndraw = 0, 0
+    if lk64 is not None and W >= 129:
+        # the posterior bulk of the SNR-2000 injection for the mixed-vs-FP64
+        # |dlogL| gate: Fisher-ball draws in every parameter the source depends
+        # on, kept where the FP64 logL >= -100 (the Gaussian approximation sends
+        # some draws along poorly constrained directions far from the bulk)
+        from paper_2501_08261_gb300 import mcmc
+        idx = list(range(15)) if cfg["precessing"] else mcmc.ALIGNED_IDX
+        ndraw = 128
+        ball = mcmc.fisher_ball(lk64, params[0].cpu().numpy(), idx, ndraw,
+                                seed=walker_seed(rank) + 5)
+        keep = torch.nonzero(lk64.loglike(ball) >= -100.0).flatten()[:64]
+        nball = int(keep.numel())
+        params[1:1 + nball] = ball[keep]
     theta = params.cpu().numpy()
     logl = torch.empty(W, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
@@ -306,6 +364,8 @@ def run_ours(args):
 
     # launch shapes measured once for this workload (lisa_td_autotune)
     tuned = api.lisa_td_autotune(lk32.ctx, params, W)
+    # the FP32 FMA rate this GPU sustains, in this process and on its clocks
+    fma_tflops = api.lisa_td_fp32_fma_rate()
     for _ in range(args.warmup):
         step32()
     torch.cuda.synchronize()
@@ -354,8 +414,16 @@ def run_ours(args):
         a64 = l64.abs().cpu().numpy()
         bulk = a64 <= 100.0
         far = ~bulk
+        ball = slice(0, 1 + nball)
+        l64h = l64.cpu().numpy()
         cmp = {"max_abs_dlogL_bulk": float(d[bulk].max()) if bulk.any() else None,
                "bulk_walkers": int(bulk.sum()),
+               "fisher_ball": {"walkers": 1 + nball, "draws": ndraw,
+                               "max_abs_dlogL": float(d[ball].max()),
+                               "logL_fp64_range": [float(l64h[ball].min()), float(l64h[ball].max())],
+                               "draw": "injection + theta ~ N(theta_inj, F^-1) in all source "
+                                       "parameters (F from the FP64 likelihood's finite "
+                                       "differences), the first 64 with FP64 logL >= -100"},
                "max_rel_dlogL_far": float((d[far] / a64[far]).max()) if far.any() else None,
                "snr_injection": 2000.0}
     # roofline of the dominant stage (alu bound, FP32)
@@ -372,7 +440,12 @@ def run_ours(args):
                 "traffic": (round(NCU_BYTES_PER_UNIT[dom] * walker_samples)
                             if NCU_BYTES_PER_UNIT.get(dom) else None),
                 "traffic_unit": "bytes per launch (ncu dram read+write, scaled from 30 d x 64 walkers)",
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal)"}
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2.07 GHz (nominal)",
+                "peak_measured": round(fma_tflops, 2),
+                "frac_of_measured": round(ach / fma_tflops, 4),
+                "peak_measured_note": "lisa_td_fp32_fma_rate: 16 independent FMA chains per "
+                                      "thread, 2048 threads per SM, best of 3, measured before "
+                                      "the timed region"}
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "logL evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32 / args.steps, 3),
@@ -417,37 +490,41 @@ def run_ours(args):
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as it stands, each step a bounded sample."""
+    """The FP64 CPU oracle as it stands, each step a bounded sample: every host
+    core (one spawned process each) evaluates one walker on a 2-day segment."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    import numpy as np
     from oracle import pipeline
     from paper_2501_08261_gb300 import workloads
     cfg = workloads.config(WORKLOAD)
     seg = 34560                                        # 2-day segment per step
-    s = pipeline.Setup(dt=cfg["dt"], n=seg, f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
-                       tdi_gen=cfg["tdi_gen"], lagrange_order=cfg["lagrange_order"],
-                       orbit="kepler", mode_mask=cfg["mode_mask"])
+    s = _oracle_segment_setup(cfg, seg)
     theta = workloads.prior_draws(1, seg, cfg["dt"], seed=1000)[0]
     d = pipeline.aet(theta, s)
-    for _ in range(args.warmup):
-        pipeline.loglike(theta, s, d)
-    t = time.perf_counter()
-    for _ in range(args.steps):
-        pipeline.loglike(theta, s, d)
-    el = time.perf_counter() - t
-    per_eval_full = el / args.steps * cfg["n"] / seg
-    v = 1.0 / per_eval_full
-    sample = (f"1 walker per step, {seg}-sample (2 d) segment of the workload, scaled by n "
-              f"to the {cfg['n']}-sample series")
+    pool, cores = _oracle_pool()
+    jobs = [(cfg, seg, theta, d)] * cores
+    try:
+        for _ in range(args.warmup):
+            pool.map(_oracle_worker, jobs, chunksize=1)
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            pool.map(_oracle_worker, jobs, chunksize=1)
+        el = time.perf_counter() - t
+    finally:
+        pool.close()
+        pool.join()
+    v = cores * args.steps / el / (cfg["n"] / seg)
+    sample = (f"{cores} walkers per step (one per host core, spawned processes), each a "
+              f"{seg}-sample (2 d) segment of the workload, scaled by n to the "
+              f"{cfg['n']}-sample series")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "logL evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(el / args.steps * 1e3, 2), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "60 d @ 5 s, HM, Keplerian, TDI 2.0 (oracle on 2-d segments)"},
-        "cpu_baseline": {"value": v, "unit": "logL evals/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": v, "unit": "logL evals/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": v, "unit": "logL evals/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}), flush=True)

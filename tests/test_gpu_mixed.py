@@ -161,28 +161,36 @@ def test_mixed_matches_fp64_gpu_at_bench_shape():
 
 def test_bench_configuration_256_walkers_autotuned():
     """The configuration bench.py times: 60 d, 256 walkers, the mixed context
-    autotuned for them (lisa_td_autotune), an SNR-2000 injection.  logL of all
-    256 walkers against the FP64 GPU path (the bulk bar 0.05, relative 1e-4
-    for far walkers), and sampled A, E, T outputs of the injection walker in
-    the tuned launch shapes against the oracle."""
+    autotuned for them (lisa_td_autotune), an SNR-2000 injection.  Walkers
+    1..64 are the posterior bulk: draws from N(theta_inj, F^-1) in all eleven
+    parameters of the aligned source (F from the FP64 likelihood) whose FP64
+    logL is >= -100, at least 32 of them.  logL of all
+    256 walkers against the FP64 GPU path (0.05 absolute on the bulk, relative
+    1e-4 for far walkers), and sampled A, E, T outputs of the injection walker
+    in the tuned launch shapes against the oracle."""
+    from paper_2501_08261_gb300 import mcmc
     cfg = workloads.config("c2_hm_60d")
     W = 256
     th = _walkers(cfg, W, 71)
     s = oracle_setup(cfg)
     truth, d = _snr_scaled(th[0], s, 2000.0)
-    th[0:8] = truth
-    th[1:8, 14] += np.linspace(-1.0, 1.0, 7)
+    th[0] = truth
+    lk64 = api.Likelihood(precision=0, max_walkers=W, **gpu_kwargs(cfg))
+    lk64.set_data(_t(d))
+    ball = mcmc.fisher_ball(lk64, truth, mcmc.ALIGNED_IDX, 128, seed=72)
+    keep = torch.nonzero(lk64.loglike(ball) >= -100.0).flatten()[:64].cpu().numpy()
+    assert len(keep) >= 32, len(keep)                    # a posterior-bulk set of >= 32
+    th[1:1 + len(keep)] = ball.cpu().numpy()[keep]
+    nb = 1 + len(keep)
+    a = lk64.loglike(_t(th)).cpu().numpy()
+    lk64.close()
     lk32 = _lik(cfg, W)
     lk32.set_data(_t(d))
     choice = api.lisa_td_autotune(lk32.ctx, _t(th), W)
     b = lk32.loglike(_t(th)).cpu().numpy()
-    lk64 = api.Likelihood(precision=0, max_walkers=W, **gpu_kwargs(cfg))
-    lk64.set_data(_t(d))
-    a = lk64.loglike(_t(th)).cpu().numpy()
-    lk64.close()
     for w, (g, o) in enumerate(zip(b, a)):
         assert abs(g - o) <= max(0.05, 1e-4 * abs(o)), (w, choice, g, o)
-    assert np.max(np.abs(b[:8] - a[:8])) <= 0.05
+    assert np.max(np.abs(b[:nb] - a[:nb])) <= 0.05
     idx = np.unique(np.concatenate([np.arange(0, 24), np.arange(cfg["n"] - 24, cfg["n"]),
                                     np.random.default_rng(5).integers(0, cfg["n"], 120)]))
     aet = lk32.tdi(lk32.project(_t(th[:1]))).cpu().numpy()[:, :, 0]

@@ -45,11 +45,16 @@ def test_ragged_walkers_windows_and_merger_times(seed):
     before_end = n * DT - th[:, 14]
     assert np.all(before_end >= 0.02 * nw * DT - 1e-6)
     assert np.all(before_end <= 0.10 * nw * DT + 1e-6)
-    # the window covers the time to merger from f_min plus the pad, unless capped at 60 d
-    for k in range(0, 256, 17):
-        tau = workloads.newtonian_time_to_merger(th[k, 0], th[k, 1], 1e-4) + 2 * workloads.DAY
-        need = min(max(tau / workloads.DAY, 1.0), 60.0)
-        assert days[k] >= need - 1e-9 or days[k] == 60
+    # windows spread over the whole 1-60 d span (log-uniform draws)
+    assert days.min() <= 2 and days.max() >= 30
+    # a window is never much longer than the signal it holds: at most the time
+    # to merger from f_min plus the pad, rounded to the nearest 7-smooth day
+    smooth = np.array(workloads.RAGGED_DAYS)
+    for k in range(256):
+        tau = workloads.newtonian_time_to_merger(th[k, 0], th[k, 1], 1e-4) + 0.25 * workloads.DAY
+        cap = min(max(tau / workloads.DAY, 1.0), 60.0)
+        nearest = smooth[np.argmin(np.abs(smooth - cap))]
+        assert days[k] <= max(nearest, cap) + 1e-9, (k, days[k], cap)
 
 
 def test_newtonian_time_to_merger_scalings():
