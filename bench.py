@@ -36,7 +36,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12                         # 80.5
 # DRAM bytes (read + write) per walker-sample of each kernel, from one ncu
 # capture of 30 d x 64 walkers; traffic scales with walker-samples.
 # Set an entry to None when its kernel changes after the capture.
-NCU_BYTES_PER_UNIT = {"tdi": None,
+NCU_BYTES_PER_UNIT = {"tdi": (844.895488e6 + 364.326144e6) / (518400 * 64),
                       "project": 1216.544000e6 / (518400 * 64)}
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -451,9 +451,13 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df32",
         "data": "synthetic (seeded prior draws; zero-noise injection)",
-        "config": {"workload": "60 d @ 5 s (n=1036800), 256 walkers/GPU, HM (5 mode pairs), "
-                               "aligned, Keplerian unequal arms, TDI 2.0 AET, Lagrange p=31, "
-                               "band 1e-4..0.02 Hz",
+        "config": {"workload": (f"{cfg['n'] * cfg['dt'] / 86400:g} d @ {cfg['dt']:g} s "
+                                f"(n={cfg['n']}), {W} walkers/GPU, "
+                                f"{'HM (5 mode pairs)' if cfg['mode_mask'] == 31 else 'mode mask ' + str(cfg['mode_mask'])}, "
+                                f"{'precessing' if cfg['precessing'] else 'aligned'}, "
+                                f"{'Keplerian unequal arms' if cfg['orbit'] == 1 else 'rigid equal arms'}, "
+                                f"TDI {cfg['tdi_gen'] / 10:.1f} AET, Lagrange p={cfg['lagrange_order']}, "
+                                f"band {cfg['f_lo']:g}..{cfg['f_hi']:g} Hz"),
                    "walkers_per_gpu": W, "n": cfg["n"],
                    "l2": "working set ~13 GB/step >> 129 MB L2 (no flush needed)"},
         "fp64_path": {"value": round(evals * k64 / (ms64 * 1e-3), 3), "unit": "logL evals/s",
