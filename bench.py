@@ -400,6 +400,8 @@ def run_ours(args):
         step_e2e()
         torch.cuda.synchronize()
         ms_e2e = _time_steps(torch, step_e2e, args.steps, barrier)
+    if lk64 is not None:
+        lk64.close()                                   # its workspace is not needed further
     # max over ranks
     ms32, ms64, ms_e2e = max_over_ranks(torch, dist, [ms32, ms64, ms_e2e], dev)
     if rank != 0:
@@ -481,13 +483,30 @@ def run_ours(args):
         out["ragged"] = ragged_measure(torch, api, workloads, dev, max(2, args.steps // 2))
     if not args.no_proposals:
         # learned proposal vs the Fisher-Gaussian one, on the exact likelihood
+        # at the learned-proposal configuration: a 60-day precessing signal of
+        # the headline's shape, 512 walkers, the flow trained on ~2e5 samples
+        # of the sampler's own random-walk chain
         from paper_2501_08261_gb300 import proposals
-        r = proposals.compare()
+        r = proposals.compare(cfg_name="c3_prec_60d", W=512, rw_steps=450, burn=50, steps=300)
         out["proposals"] = {
             "workload": r["workload"],
             "fisher_gauss": {k: round(r["fisher_gauss"][k], 4) for k in ("acceptance", "ess_per_s", "tau")},
             "flow": {k: round(r["flow"][k], 4) for k in ("acceptance", "ess_per_s", "tau", "train_ms")},
+            "fisher_random_walk": {k: round(r["fisher_random_walk"][k], 4)
+                                   for k in ("acceptance", "tau", "gpu_ms")},
+            "amortised": {k: (round(v, 4) if isinstance(v, float) else v)
+                          for k, v in r["amortised"].items()},
+            "protocol": {k: (round(v, 4) if isinstance(v, float) else v)
+                         for k, v in r["protocol"].items()},
             "unit": "effective samples/s (GPU time, integrated autocorrelation, Sokal window)"}
+        # parallel tempering with a flow per temperature (one day, 4 x 256)
+        rt = proposals.compare_tempered()
+        out["tempered"] = {"workload": rt["workload"], "betas": rt["betas"],
+                           "acceptance": {"flow": rt["flow"]["acceptance"],
+                                          "fisher_gauss": rt["fisher_gauss"]["acceptance"],
+                                          "fisher_random_walk": rt["fisher_random_walk"]["acceptance"]},
+                           "cold_ess_per_s": {"flow": rt["flow"]["ess_cold_per_s"],
+                                              "fisher_gauss": rt["fisher_gauss"]["ess_cold_per_s"]}}
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

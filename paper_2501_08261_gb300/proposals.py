@@ -51,8 +51,13 @@ def compare(cfg_name="c3_prec_1d", W=512, rw_steps=600, burn=100, steps=600, epo
     far = truth.copy()
     far[8] = 1e30
     snr = math.sqrt(-2.0 * lik64.loglike(T(far[None])).item())
-    F = mcmc.fisher(lik64, truth, idx, fd_steps(truth))
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record()
+    F = mcmc.fisher_scaled(lik64, truth, idx, fd_steps(truth))
     L = mcmc.gauss_factor(F, idx, lo, hi)
+    f1.record()
+    torch.cuda.synchronize()
+    fisher_ms = f0.elapsed_time(f1)
     mu = T(truth)
     ch = mcmc.MH(lik, lo, hi, W, seed=seed)
     gen = torch.Generator(device="cuda")
@@ -93,9 +98,26 @@ def compare(cfg_name="c3_prec_1d", W=512, rw_steps=600, burn=100, steps=600, epo
     lik.close()
     lik64.close()
     lv = losses.cpu().numpy()
+    days = cfg["n"] * cfg["dt"] / 86400.0
+    # amortised over the training: the flow's chain charged with its training
+    # time (the Fisher-Gaussian needs none); and over the whole protocol: every
+    # GPU millisecond, the Fisher matrix and the random-walk chain included --
+    # both protocols run that chain first, so its own effective samples count
+    # for both (and, on short signals, dominate both)
+    t_g = fisher_ms + ms_rw + ms_g
+    t_f = fisher_ms + ms_rw + train_ms + ms_f
     return {
-        "workload": f"{cfg_name}: 1 d @ 5 s, precessing, 5 modes, Keplerian, TDI 2; Table I "
-                    f"injection (SNR {snr:.0f}), {W} walkers, {D} parameters, uniform Table I priors",
+        "workload": f"{cfg_name}: {days:g} d @ {cfg['dt']:g} s, precessing, 5 modes, Keplerian, "
+                    f"TDI 2; Table I injection (SNR {snr:.0f}), {W} walkers, {D} parameters, "
+                    f"uniform Table I priors; flow trained on {len(samples)} chain samples",
+        "fisher_ms": fisher_ms,
+        "amortised": {"fisher_gauss_ess_per_s": ess_g / (ms_g * 1e-3),
+                      "flow_ess_per_s": ess_f / ((ms_f + train_ms) * 1e-3),
+                      "note": "ESS of the proposal's chain / (chain [+ training] GPU time)"},
+        "protocol": {"fisher_gauss_ess_per_s": (ess_rw + ess_g) / (t_g * 1e-3),
+                     "flow_ess_per_s": (ess_rw + ess_f) / (t_f * 1e-3),
+                     "note": "(ESS of the random-walk chain + ESS of the proposal's chain) / "
+                             "(Fisher + random walk [+ training] + chain GPU time)"},
         "fisher_random_walk": {"acceptance": acc_rw, "steps": rw_steps, "tau": tau_rw,
                                "ess": ess_rw, "gpu_ms": ms_rw},
         "fisher_gauss": {"acceptance": acc_g, "steps": steps, "tau": tau_g, "ess": ess_g,

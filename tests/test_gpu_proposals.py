@@ -1,7 +1,8 @@
 """The learned proposal against the method without it (Sec. II.C's
 Fisher-Gaussian): on the exact likelihood of a one-day precessing signal, the
 flow trained on the sampler's own chain must accept more often and give more
-effective samples per second than N(theta_inj, F^-1)."""
+effective samples per second than N(theta_inj, F^-1), per chain and with the
+flow's training time charged to its chain."""
 import numpy as np
 import pytest
 
@@ -18,3 +19,10 @@ def test_flow_proposal_beats_fisher_gaussian():
     assert np.isfinite(f["loss_first_last"]).all() and f["loss_first_last"][1] < f["loss_first_last"][0]
     assert f["acceptance"] > 1.3 * g["acceptance"], r
     assert f["ess_per_s"] > 1.5 * g["ess_per_s"], r
+    # and with the flow charged for its training.  Over the whole protocol
+    # (Fisher matrix, the random walk that trains the flow, training, chain) the
+    # figures are reported but not asserted: both protocols run the same random
+    # walk first, and on this one-day signal its own effective samples dominate
+    # both totals, so they differ by a few per cent either way
+    a = r["amortised"]
+    assert a["flow_ess_per_s"] > 1.5 * a["fisher_gauss_ess_per_s"], r
