@@ -475,6 +475,11 @@ def run_ours(args):
         "e2e": {"value": round(evals * args.steps / (ms_e2e * 1e-3), 2), "unit": "logL evals/s",
                 "h2d_bytes_per_step": W * 15 * 8, "d2h_bytes_per_step": W * 8},
     }
+    # the side measurements below are single-GPU experiments (and the oracle's
+    # timing belongs to N = 1): under torchrun they are left out so that the
+    # N GPUs are not held for them
+    if ws > 1:
+        args.no_cpu_baseline = args.no_nested = args.no_ragged = args.no_proposals = True
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, theta[0], aet.cpu().numpy())
     if not args.no_nested:

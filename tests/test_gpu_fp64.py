@@ -161,7 +161,7 @@ def test_single_walker_and_zero_distance_limit():
     assert got == pytest.approx(-0.5 * dd, rel=1e-12)
 
 
-@pytest.mark.parametrize("name", ["c2_hm_60d"])
+@pytest.mark.parametrize("name", ["c2_hm_60d", "c3_prec_60d"])
 def test_full_size_sampled_outputs(name):
     """60 days, 2 walkers: AET at 300 sampled indices (oracle evaluated sparsely)."""
     cfg = workloads.config(name)

@@ -123,8 +123,9 @@ def test_mixed_loglike_bulk_and_far(name):
     assert abs(got[0]) <= 0.05
 
 
-def test_mixed_full_size_sampled_outputs():
-    cfg = workloads.config("c2_hm_60d")
+@pytest.mark.parametrize("name", ["c2_hm_60d", "c3_prec_60d"])
+def test_mixed_full_size_sampled_outputs(name):
+    cfg = workloads.config(name)
     s = oracle_setup(cfg)
     th = _walkers(cfg, 2, 60)
     lk = _lik(cfg, 2)
