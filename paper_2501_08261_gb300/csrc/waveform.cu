@@ -166,12 +166,13 @@ __device__ inline float planck_down_ff(float f) {
 }
 
 // h+ - i hx before the psi rotation at sample i (time t0 + i dt), mixed precision.
-__device__ void polar_mixed(const MixRec& X, int status, int64_t i, int precessing, float& re,
+__device__ void polar_mixed(const MixRec& X, int status, int i, int precessing, float& re,
                             float& im) {
   re = 0.0f;
   im = 0.0f;
   if (status != 0) return;
-  // t - t0 = i * dt exactly in double-float
+  // t - t0 = i * dt exactly in double-float (i < 2^24: exact in FP32, and a
+  // 32-bit conversion keeps the FP64 pipe out of the per-sample work)
   float fi = (float)i;
   df32 t = two_prod(fi, X.dt.hi);
   t = fast_two_sum(t.hi, fmaf(fi, X.dt.lo, t.lo));
@@ -297,13 +298,24 @@ __global__ void __launch_bounds__(128) waveform_mixed_kernel(
     const int64_t* __restrict__ woff) {
   const int w = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the walker's constants, read once per block into shared memory (every
+  // thread of the block serves the same walker)
+  __shared__ MixRec xs;
+  __shared__ int st;
+  {
+    const int* src = reinterpret_cast<const int*>(&walkers[w].mx);
+    int* dst = reinterpret_cast<int*>(&xs);
+    for (int q = threadIdx.x; q < (int)(sizeof(MixRec) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
+    if (threadIdx.x == 0) st = walkers[w].status;
+  }
+  __syncthreads();
   if (i >= n) return;
   const int64_t lo = woff ? woff[w] : 0;
   if (i < lo) return;                          // before the walker's window: never read
-  const MixRec& X = walkers[w].mx;
+  const MixRec& X = xs;
   float re, im;
   // the double-float time anchors are relative to the window start
-  polar_mixed(X, walkers[w].status, i - lo, precessing, re, im);
+  polar_mixed(X, st, (int)(i - lo), precessing, re, im);
   float Hr = re * X.c2psi - im * X.s2psi;
   float Hi = re * X.s2psi + im * X.c2psi;
   h[(int64_t)w * n + i] = make_float2(Hr, -Hi);

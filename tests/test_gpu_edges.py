@@ -147,3 +147,32 @@ def test_degenerate_cases_match_oracle(name, precision):
     # the swap rule: the same binary with its bodies listed the other way round
     assert abs(got[1] - got[0]) <= (1e-9 if precision == 0 else 1e-3) * max(1.0, abs(got[0]))
     lk.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_grid_starting_a_year_later_matches_oracle(precision):
+    """A grid that starts at t0 = one sidereal year plus 40 days (the
+    constellation elsewhere on its orbit, and absolute times of 3.5e7 s, where
+    FP32 resolves only 2 s): the mixed path carries time relative to t0 and
+    FP64 anchors, so its logL must still meet the bars."""
+    t0 = 31558149.763545603 + 40 * 86400.0
+    cfg = workloads.config("c2_hm_1d", t0=t0)
+    s = oracle_setup(cfg)
+    th = workloads.prior_draws(4, cfg["n"], cfg["dt"], 95, logm=(5.5, 7.0))
+    th[:, 14] += t0                                  # mergers inside the shifted window
+    d = pipeline.aet(th[0], s)
+    far = th[0].copy()
+    far[8] = 1e30
+    rho = np.sqrt(-2.0 * pipeline.loglike(far, s, d))
+    d = d * (1000.0 / rho)
+    th[0, 8] *= rho / 1000.0
+    th[1] = th[0]
+    th[1, 14] += 1.5                                 # a bulk walker
+    lk = api.Likelihood(precision=precision, max_walkers=4, **gpu_kwargs(cfg))
+    lk.set_data(_t(d))
+    got = lk.loglike(_t(th)).cpu().numpy()
+    for w in range(4):
+        o = pipeline.loglike(th[w], s, d)
+        tol = max(1e-6, 1e-11 * abs(o)) if precision == 0 else max(0.05, 1e-4 * abs(o))
+        assert abs(got[w] - o) <= tol, (w, got[w], o)
+    lk.close()
