@@ -173,6 +173,9 @@ def test_grid_starting_a_year_later_matches_oracle(precision):
     got = lk.loglike(_t(th)).cpu().numpy()
     for w in range(4):
         o = pipeline.loglike(th[w], s, d)
-        tol = max(1e-6, 1e-11 * abs(o)) if precision == 0 else max(0.05, 1e-4 * abs(o))
+        # FP64: absolute times near 3.5e7 s carry about 500 times the rounding of the
+        # one-day grids at t0 = 0 (ulp 7.5e-9 s), in the oracle and the GPU alike,
+        # so the relative part of the bar scales from 1e-11 to 1e-8
+        tol = max(1e-6, 1e-8 * abs(o)) if precision == 0 else max(0.05, 1e-4 * abs(o))
         assert abs(got[w] - o) <= tol, (w, got[w], o)
     lk.close()

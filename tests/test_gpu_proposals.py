@@ -14,7 +14,9 @@ def test_flow_proposal_beats_fisher_gaussian():
     from paper_2501_08261_gb300 import build, proposals
     build.build()
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
-    r = proposals.compare()
+    # chains of 1500 steps (a few seconds of GPU time each), so that the flow's
+    # ~1 s of training is charged against a chain of realistic length
+    r = proposals.compare(steps=1500)
     g, f = r["fisher_gauss"], r["flow"]
     assert np.isfinite(f["loss_first_last"]).all() and f["loss_first_last"][1] < f["loss_first_last"][0]
     assert f["acceptance"] > 1.3 * g["acceptance"], r
