@@ -298,24 +298,13 @@ __global__ void __launch_bounds__(128) waveform_mixed_kernel(
     const int64_t* __restrict__ woff) {
   const int w = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // the walker's constants, read once per block into shared memory (every
-  // thread of the block serves the same walker)
-  __shared__ MixRec xs;
-  __shared__ int st;
-  {
-    const int* src = reinterpret_cast<const int*>(&walkers[w].mx);
-    int* dst = reinterpret_cast<int*>(&xs);
-    for (int q = threadIdx.x; q < (int)(sizeof(MixRec) / sizeof(int)); q += blockDim.x) dst[q] = src[q];
-    if (threadIdx.x == 0) st = walkers[w].status;
-  }
-  __syncthreads();
   if (i >= n) return;
   const int64_t lo = woff ? woff[w] : 0;
   if (i < lo) return;                          // before the walker's window: never read
-  const MixRec& X = xs;
+  const MixRec& X = walkers[w].mx;
   float re, im;
   // the double-float time anchors are relative to the window start
-  polar_mixed(X, st, (int)(i - lo), precessing, re, im);
+  polar_mixed(X, walkers[w].status, (int)(i - lo), precessing, re, im);
   float Hr = re * X.c2psi - im * X.s2psi;
   float Hi = re * X.s2psi + im * X.c2psi;
   h[(int64_t)w * n + i] = make_float2(Hr, -Hi);
