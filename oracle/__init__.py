@@ -25,6 +25,10 @@ Module map (paper section / equation each follows):
 * ``likelihood`` DFT, Sangria PSD, matched-filter inner product and logL
                  (Sec. II.B, end).
 * ``pipeline``   parameters -> A,E,T -> logL for one walker.
+* ``heterodyne`` the heterodyned time-domain likelihood (the speed-up route
+                 the paper names in Sec. I and Sec. IV, defined in the module):
+                 analytic mode polarisations, the continuous-time response at
+                 nodes, fiducial carriers and the interpolated model.
 
 Parity status: everything here is pinned by ``tests/test_oracle_*.py`` to
 closed forms, invariants, brute force or special cases, EXCEPT the absolute

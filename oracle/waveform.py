@@ -129,6 +129,25 @@ def planck_fall_freq(f):
     return out
 
 
+def mode_phase(src, l, m, t):
+    """Phase Phi_lm(t) and angular frequency of mode (l, m > 0), h_lm = A e^{-i Phi}:
+    m phi(u) in the inspiral, the C1-continuous ringdown phase after t_m."""
+    t = np.asarray(t, dtype=np.float64)
+    M, nu = src["M"], src["nu"]
+    um, tm, tau_d = src["um"], src["tm"], src["tau_d"]
+    insp = t < tm
+    x = np.where(insp, nu * (src["tc"] - t) / (5.0 * M), K.X_MERGE)
+    u = x ** 0.125
+    om, ph = _omega_phase(src, u)
+    om_m, ph_m = _omega_phase(src, um)
+    w_rd = K.RD_RATIO[(l, m)] * src["w_rd22"]
+    tau = np.maximum(t - tm, 0.0)
+    decay_f = np.exp(-tau / tau_d)
+    phase_r = m * ph_m + w_rd * tau + (m * om_m - w_rd) * tau_d * (1.0 - decay_f)
+    freq_r = w_rd + (m * om_m - w_rd) * decay_f
+    return np.where(insp, m * ph, phase_r), np.where(insp, m * om, freq_r)
+
+
 def mode(src, l, m, t, t0):
     """Complex mode h_lm(t) (m > 0) of the aligned / co-precessing stand-in."""
     t = np.asarray(t, dtype=np.float64)
@@ -141,25 +160,19 @@ def mode(src, l, m, t, t0):
     insp = t < tm
     x = np.where(insp, nu * (src["tc"] - t) / (5.0 * M), K.X_MERGE)
     u = x ** 0.125
-    om, ph = _omega_phase(src, u)
+    om, _ = _omega_phase(src, u)
     amp_i = pref * (M * om) ** p
-    phase_i = m * ph
-    freq_i = m * om
 
     # ringdown, C1-continuous at t_m
-    om_m, ph_m = _omega_phase(src, um)
+    om_m, _ = _omega_phase(src, um)
     A_m = pref * (M * om_m) ** p
     a_lm = p * _omega_dot(src, um) / om_m + 1.0 / tau_d
-    w_rd = K.RD_RATIO[(l, m)] * src["w_rd22"]
     tau = np.maximum(t - tm, 0.0)
     decay_f = np.exp(-tau / tau_d)
-    phase_r = m * ph_m + w_rd * tau + (m * om_m - w_rd) * tau_d * (1.0 - decay_f)
-    freq_r = w_rd + (m * om_m - w_rd) * decay_f
     amp_r = A_m * (1.0 + a_lm * tau) * decay_f
 
     amp = np.where(insp, amp_i, amp_r)
-    phase = np.where(insp, phase_i, phase_r)
-    freq = np.where(insp, freq_i, freq_r)
+    phase, freq = mode_phase(src, l, m, t)
     t_a = max(t0, src["t_start"])
     win = np.where(t >= src["t_start"], planck_rise(t, t_a, K.T_TAPER), 0.0)
     win = win * planck_fall_freq(freq / (2.0 * math.pi))

@@ -193,3 +193,42 @@ def table1_prior_box(tc, tc_halfwidth=600.0):
 def standard_normals(w, dim, seed):
     """Standard normal draws (used as z in theta + L z perturbations)."""
     return np.random.default_rng(seed).normal(size=(w, dim))
+
+
+def heterodyne_nodes(n, dt, m1, m2, tc, t0=0.0, df=2e-5, dt_max=3600.0, x_dense=6.0,
+                     sky_pad=520.0, ring_m=200.0):
+    """Node indices of the heterodyned likelihood for a fiducial of masses m1, m2
+    [Msun] and merger parameter tc [s] on an n-sample grid.
+
+    Rule (an input choice, like the grid): a node at every sample from the
+    Newtonian x = nu (tc - t) / (5 M) = x_dense through ring_m total masses
+    after tc, widened by sky_pad seconds on both sides (the largest light time
+    from the Sun to the constellation plus the arm); elsewhere the next node
+    follows when the Newtonian (2,2) frequency has advanced by df [Hz], at
+    least one and at most dt_max seconds later.  Always holds 0 and n - 1."""
+    mt = (m1 + m2) * 4.925490947641267e-06
+    nu = m1 * m2 / (m1 + m2) ** 2
+    mc = mt * nu ** 0.6
+    a = tc - 5.0 * mt * x_dense / nu - sky_pad
+    b = tc + ring_m * mt + sky_pad
+    ia = max(0, int(math.floor((a - t0) / dt)))
+    ib = min(n - 1, int(math.ceil((b - t0) / dt)))
+    out = [0]
+    i = 0
+    while i < n - 1:
+        if ia <= i < ib:
+            step = 1
+        else:
+            tau = tc - (t0 + i * dt)
+            if tau > 0.0:
+                f = (5.0 / (256.0 * tau)) ** 0.375 * mc ** -0.625 / math.pi
+                fdot = 96.0 / 5.0 * math.pi ** (8.0 / 3.0) * mc ** (5.0 / 3.0) * f ** (11.0 / 3.0)
+                sec = min(max(df / fdot, dt), dt_max)
+            else:
+                sec = dt_max
+            step = max(1, int(sec // dt))
+            if i < ia < i + step:
+                step = ia - i
+        i = min(i + step, n - 1)
+        out.append(i)
+    return np.array(out, dtype=np.int64)
