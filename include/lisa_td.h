@@ -242,6 +242,56 @@ int lisa_td_fp32_fma_rate(double* tflops_host, void* stream);
 int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_dev, int32_t W,
                                      double* logl_dev, void* stream);
 
+/* Heterodyned time-domain likelihood.  The paper names heterodyning and
+ * relative binning as the route to cheaper likelihoods (Sec. I, Sec. IV) and
+ * gives no time-domain form; this is the library's:
+ *   - every mode pair j = (l, +-m) is written as an analytic signal whose real
+ *     part is the pair's h+ (hx) and whose phase is the mode's own
+ *     e^{-i Phi_lm}; its TDI channel c in continuous time (waveform at the
+ *     exact emission and reception times of Eq. yslr, delays as in the TDI
+ *     equations, link geometry at the delayed times) is X_jc(t; theta);
+ *   - with a fiducial theta0, carriers C_j(t) = e^{-i Phi_lm(t; theta0)} and
+ *     nodes 0 = i_0 < ... < i_{B-1} = n - 1, the node differences are
+ *     dZ_jc,b = conj(C_j(t_b)) (X_jc(t_b; theta) - X_jc(t_b; theta0));
+ *   - the model on the grid is X0_c(t_i) + Re sum_j C_j(t_i) lerp_b(dZ_jc)(t_i),
+ *     X0 = Re sum_j X_jc(t_i; theta0) (computed once in FP64), and logL is the
+ *     full likelihood's DFT + PSD-weighted norm of model - data.
+ * At theta0 the model is X0 exactly; with a node at every sample it is the
+ * continuous-time response of theta.  Only the B nodes pay for the waveform and
+ * response (96 waveform evaluations per node for TDI 2); the grid pays a
+ * complex multiply-add per mode and channel.
+ *
+ * lisa_td_het_setup: fiducial theta0_host [15] (host), nodes_host [B] (host,
+ * int64 sample indices rising strictly from 0 to n - 1, B >= 2).  Computes
+ * the fiducial's carriers, X0 and node values; replaces an earlier set-up.
+ * Allocates about n (3 x 28 + nmodes x 24) + B x (48 x 160 + nmodes x 24 x
+ * (max_walkers + 1)) bytes; synchronises `stream`.  LISA_TD_EINVAL for NULL
+ * pointers, bad nodes or an invalid fiducial (the prep checks of
+ * lisa_td_loglike_batch), LISA_TD_ENOMEM, LISA_TD_ECUDA.  Every orbit kind,
+ * TDI generation and delay form of the context is supported; ragged batches
+ * are not.
+ *
+ * lisa_td_het_loglike: as lisa_td_loglike_batch (same arguments, data and
+ * status semantics) with the heterodyned model; LISA_TD_EINVAL before
+ * lisa_td_het_setup or lisa_td_set_data.  Stage profiling (lisa_td_profile)
+ * records: 0 prep, 1 node differences, 2 expansion to the grid + residual,
+ * 3 (empty), 4 FFT pass 1, 5 FFT pass 2 + norm, 6 reduction.
+ *
+ * lisa_td_het_deltas: the node differences dZ of W walkers, written to
+ * dz_dev [B][nmodes][3][W] complex (double2 for precision 0, float2 for 1),
+ * modes in mask order, channels A, E, T.
+ * lisa_td_het_aet: the heterodyned model A, E, T of W walkers, written to
+ * aet_dev [3][n][W] (double / float).
+ * Both need lisa_td_het_setup; neither needs data. */
+int lisa_td_het_setup(lisa_td_ctx* ctx, const double* theta0_host, const int64_t* nodes_host,
+                      int64_t B, void* stream);
+int lisa_td_het_loglike(lisa_td_ctx* ctx, const double* params_dev, int32_t W, double* logl_dev,
+                        int32_t* status_dev, void* stream);
+int lisa_td_het_deltas(lisa_td_ctx* ctx, const double* params_dev, int32_t W, void* dz_dev,
+                       void* stream);
+int lisa_td_het_aet(lisa_td_ctx* ctx, const double* params_dev, int32_t W, void* aet_dev,
+                    void* stream);
+
 void lisa_td_destroy(lisa_td_ctx* ctx);
 const char* lisa_td_last_error(void);
 

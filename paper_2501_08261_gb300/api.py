@@ -15,7 +15,8 @@ ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ERANGE"}
 EXPORTS = ("lisa_td_create", "lisa_td_create_orbits", "lisa_td_set_data", "lisa_td_waveform", "lisa_td_project",
            "lisa_td_tdi", "lisa_td_loglike_batch", "lisa_td_profile", "lisa_td_profile_read",
            "lisa_td_destroy", "lisa_td_last_error", "lisa_td_residual_loglike_noalloc",
-           "lisa_td_fp32_fma_rate",
+           "lisa_td_fp32_fma_rate", "lisa_td_het_setup", "lisa_td_het_loglike",
+           "lisa_td_het_deltas", "lisa_td_het_aet",
            "lisa_td_loglike_ragged", "lisa_td_ragged_graph", "lisa_td_autotune", "lisa_td_noise",
            "lisa_fisher_npoints", "lisa_fisher_points", "lisa_fisher_assemble", "lisa_cholesky",
            "lisa_gauss_draw", "lisa_gauss_logq", "lisa_gauss_walk", "lisa_mh_accept", "lisa_pt_swap",
@@ -67,6 +68,10 @@ def load_library(path=None):
                                  ctypes.c_int),
         "lisa_td_residual_loglike_noalloc": ([ctypes.POINTER(Config), P, I32, P, P], ctypes.c_int),
         "lisa_td_fp32_fma_rate": ([ctypes.POINTER(ctypes.c_double), P], ctypes.c_int),
+        "lisa_td_het_setup": ([P, P, P, I64, P], ctypes.c_int),
+        "lisa_td_het_loglike": ([P, P, I32, P, P, P], ctypes.c_int),
+        "lisa_td_het_deltas": ([P, P, I32, P, P], ctypes.c_int),
+        "lisa_td_het_aet": ([P, P, I32, P, P], ctypes.c_int),
         "lisa_fisher_npoints": ([I32], ctypes.c_int),
         "lisa_fisher_points": ([P, P, P, I32, P, P], ctypes.c_int),
         "lisa_fisher_assemble": ([P, P, I32, P, P], ctypes.c_int),
@@ -179,6 +184,34 @@ def lisa_td_tdi(ctx, y, W, aet, stream=None):
 def lisa_td_loglike_batch(ctx, params, W, logl, status=None, stream=None):
     _check(lib().lisa_td_loglike_batch(ctx, _ptr(params), int(W), _ptr(logl), _ptr(status),
                                        _stream(stream)), "lisa_td_loglike_batch")
+
+
+def lisa_td_het_setup(ctx, theta0, nodes, stream=None):
+    """Heterodyned likelihood set-up: fiducial theta0 [15] and node indices
+    (host arrays)."""
+    import numpy as np
+    th = np.ascontiguousarray(theta0, dtype=np.float64).reshape(-1)
+    nd = np.ascontiguousarray(nodes, dtype=np.int64).reshape(-1)
+    if th.size != 15:
+        raise ValueError("theta0 must hold 15 parameters")
+    _check(lib().lisa_td_het_setup(ctx, th.ctypes.data_as(ctypes.c_void_p),
+                                   nd.ctypes.data_as(ctypes.c_void_p), int(nd.size),
+                                   _stream(stream)), "lisa_td_het_setup")
+
+
+def lisa_td_het_loglike(ctx, params, W, logl, status=None, stream=None):
+    _check(lib().lisa_td_het_loglike(ctx, _ptr(params), int(W), _ptr(logl), _ptr(status),
+                                     _stream(stream)), "lisa_td_het_loglike")
+
+
+def lisa_td_het_deltas(ctx, params, W, dz, stream=None):
+    _check(lib().lisa_td_het_deltas(ctx, _ptr(params), int(W), _ptr(dz), _stream(stream)),
+           "lisa_td_het_deltas")
+
+
+def lisa_td_het_aet(ctx, params, W, aet, stream=None):
+    _check(lib().lisa_td_het_aet(ctx, _ptr(params), int(W), _ptr(aet), _stream(stream)),
+           "lisa_td_het_aet")
 
 
 def lisa_td_loglike_ragged(ctx, params, W, n_per_walker, logl, status=None, stream=None):
@@ -454,3 +487,34 @@ class Likelihood:
         st = self.torch.empty(W, dtype=self.torch.int32, device=params.device)
         lisa_td_loglike_batch(self.ctx, params, W, out, st)
         return (out, st) if with_status else out
+
+    # heterodyned likelihood (lisa_td_het_*)
+    def het_setup(self, theta0, nodes):
+        import numpy as np
+        self.het_nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        self.het_nm = bin(self.cfg.mode_mask).count("1")
+        lisa_td_het_setup(self.ctx, theta0, self.het_nodes)
+
+    def het_loglike(self, params, with_status=False):
+        params = self._params(params)
+        W = params.shape[0]
+        out = self.torch.empty(W, dtype=self.torch.float64, device=params.device)
+        st = self.torch.empty(W, dtype=self.torch.int32, device=params.device)
+        lisa_td_het_loglike(self.ctx, params, W, out, st)
+        return (out, st) if with_status else out
+
+    def het_deltas(self, params):
+        """Node differences [B][n_modes][3][W] as a complex tensor."""
+        params = self._params(params)
+        W = params.shape[0]
+        B = self.het_nodes.size
+        dz = self.torch.empty((B, self.het_nm, 3, W, 2), dtype=self.dtype, device=params.device)
+        lisa_td_het_deltas(self.ctx, params, W, dz)
+        return self.torch.view_as_complex(dz)
+
+    def het_aet(self, params):
+        params = self._params(params)
+        W = params.shape[0]
+        aet = self.torch.empty((3, self.cfg.n, W), dtype=self.dtype, device=params.device)
+        lisa_td_het_aet(self.ctx, params, W, aet)
+        return aet

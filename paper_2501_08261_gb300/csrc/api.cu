@@ -36,6 +36,7 @@ int cuda_fail(cudaError_t e, const char* where) {
 void free_ctx(lisa_td_ctx* c) {
   if (!c) return;
   lisa::free_ragged(c);
+  lisa::free_het(c);
   if (c->prof_ev) {
     for (int q = 0; q < LISA_TD_PROF_CALLS * (LISA_TD_NSTAGE + 1); ++q)
       if (c->prof_ev[q]) cudaEventDestroy(c->prof_ev[q]);

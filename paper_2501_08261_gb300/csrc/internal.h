@@ -83,6 +83,8 @@ struct lisa_td_ctx {
   // of FFT pass 1 and pass 2
   int tune_tile, tune_warps, tune_pb1, tune_pb2;
   int tune_bs1, tune_bs2;          // FFT threads per block (0: 512)
+  // heterodyned likelihood (heterodyne.cu): fiducial tables and node workspace
+  void* het;
 };
 
 namespace lisa {
@@ -128,5 +130,7 @@ cudaError_t launch_tdi_tiles(const lisa_td_ctx* c, cudaStream_t s);
 // combined per-(channel, link) FIR weights of the mixed TDI; sets *c->tdi_flag
 // when a pair needs more than kGMax taps
 cudaError_t launch_tdi_pairs(const lisa_td_ctx* c, cudaStream_t s);
+// heterodyne.cu: release the heterodyned likelihood's tables of a context
+void free_het(lisa_td_ctx* c);
 
 }  // namespace lisa

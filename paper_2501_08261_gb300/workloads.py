@@ -196,16 +196,19 @@ def standard_normals(w, dim, seed):
 
 
 def heterodyne_nodes(n, dt, m1, m2, tc, t0=0.0, df=2e-5, dt_max=3600.0, x_dense=6.0,
-                     sky_pad=520.0, ring_m=200.0):
+                     sky_pad=520.0, ring_m=200.0, f_start=1e-4, taper=1.0e4, taper_step=250.0):
     """Node indices of the heterodyned likelihood for a fiducial of masses m1, m2
     [Msun] and merger parameter tc [s] on an n-sample grid.
 
     Rule (an input choice, like the grid): a node at every sample from the
     Newtonian x = nu (tc - t) / (5 M) = x_dense through ring_m total masses
     after tc, widened by sky_pad seconds on both sides (the largest light time
-    from the Sun to the constellation plus the arm); elsewhere the next node
-    follows when the Newtonian (2,2) frequency has advanced by df [Hz], at
-    least one and at most dt_max seconds later.  Always holds 0 and n - 1."""
+    from the Sun to the constellation plus the arm); a node every taper_step
+    seconds over the first `taper` seconds of the signal (from the later of t0
+    and the time its Newtonian (2,2) frequency is f_start), where the start
+    taper shapes the envelope; elsewhere the next node follows when the
+    Newtonian (2,2) frequency has advanced by df [Hz], at least one and at most
+    dt_max seconds later.  Always holds 0 and n - 1."""
     mt = (m1 + m2) * 4.925490947641267e-06
     nu = m1 * m2 / (m1 + m2) ** 2
     mc = mt * nu ** 0.6
@@ -231,4 +234,9 @@ def heterodyne_nodes(n, dt, m1, m2, tc, t0=0.0, df=2e-5, dt_max=3600.0, x_dense=
                 step = ia - i
         i = min(i + step, n - 1)
         out.append(i)
-    return np.array(out, dtype=np.int64)
+    ts = max(t0, tc - newtonian_time_to_merger(m1, m2, f_start))
+    i0 = int(math.floor((ts - t0) / dt))
+    i1 = int(math.ceil((ts + taper - t0) / dt))
+    k = max(1, int(taper_step // dt))
+    extra = [j for j in range(i0, i1 + 1, k) if 0 <= j < n]
+    return np.unique(np.array(out + extra, dtype=np.int64))

@@ -1,0 +1,209 @@
+"""GPU parity of the heterodyned time-domain likelihood (lisa_td_het_*) with
+the oracle's definition in ``oracle/heterodyne.py``: node differences, the
+expanded model and logL, FP64 and mixed, aligned and precessing, TDI 1.5 /
+2.0 with summed and nested delays, rigid and Keplerian orbits; the fiducial
+reproduced bit for bit; a node at every sample; the 60-day grid on sampled
+nodes."""
+import numpy as np
+import pytest
+
+from oracle import heterodyne as H
+from oracle import likelihood, pipeline
+from paper_2501_08261_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DAY = 86400.0
+ORBITS = {0: "rigid", 1: "kepler"}
+
+# Bars.  Both precisions evaluate the node values in FP64 (FP32 node sums
+# leave rounding that the TDI combinations, T above all, do not cancel).  The
+# GPU and the oracle evaluate the same continuous-time response and differ by
+# FP64 rounding (phases ~1e4 rad to ~1e-12 rad, amplified by the
+# h(t_s) - h(t_r) and TDI cancellations; measured <= 6e-11 of a channel's
+# largest node value): 1e-9.  The mixed path rounds each node difference
+# (at most twice the channel's largest value) to FP32 once: 3e-7.
+FP64_BAR, MIXED_BAR = 1e-9, 3e-7
+
+
+def _setup_pair(name, precision, walkers, n=None, **over):
+    from paper_2501_08261_gb300 import api
+    cfg = wl.config(name, **over)
+    if n is not None:
+        cfg["n"] = n
+    s = pipeline.Setup(dt=cfg["dt"], n=cfg["n"], t0=cfg["t0"], f_lo=cfg["f_lo"],
+                       f_hi=cfg["f_hi"], tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
+                       lagrange_order=cfg["lagrange_order"], orbit=ORBITS[cfg["orbit"]],
+                       mode_mask=cfg["mode_mask"], precessing=bool(cfg["precessing"]),
+                       tdi_nested=bool(cfg.get("tdi_nested", 0)))
+    lk = api.Likelihood(precision=precision, max_walkers=walkers, **cfg)
+    return s, lk
+
+
+def _theta0(precessing, tc):
+    th = wl.c1_point(3)
+    th[8] = 20.0
+    th[14] = tc
+    if precessing:
+        th[2], th[3], th[4] = 0.6, 1.0, 0.5
+        th[5], th[6], th[7] = 0.3, 2.0, 1.0
+    return th
+
+
+def _walkers(th0, rng, w):
+    """The fiducial, posterior-width offsets in all parameters and a few far ones."""
+    out = [th0.copy()]
+    width = np.array([2e-5 * th0[0], 2e-5 * th0[1], 1e-3, 1e-3, 1e-3, 1e-3, 1e-3, 1e-3,
+                      1e-3 * th0[8], 1e-3, 1e-3, 1e-4, 1e-4, 1e-3, 0.05])
+    for k in range(1, w):
+        far = 30.0 if k >= w - 2 else 1.0
+        q = th0 + far * width * rng.standard_normal(15)
+        out.append(q)
+    return np.array(out)
+
+
+def _gpu(a):
+    return torch.tensor(a, dtype=torch.float64, device="cuda")
+
+
+def _compare_deltas(got, s, walkers, th0, nodes, bar):
+    """got: complex [B][nm][3][W] from the GPU; oracle per walker."""
+    worst = 0.0
+    for w, th in enumerate(walkers):
+        ref = H.node_deltas(th, th0, s, nodes)                  # [nm][3][B]
+        scale = np.abs(H.point_aet(th, s, s.t0 + nodes * s.dt)).max(axis=(0, 2))
+        g = np.transpose(got[:, :, :, w], (1, 2, 0))
+        for c in range(3):
+            e = np.max(np.abs(g[:, c, :] - ref[:, c, :])) / scale[c]
+            worst = max(worst, e)
+            assert e <= bar, (w, c, e)
+    return worst
+
+
+CASES = [  # name, overrides, precessing
+    ("c2_hm_1d", {}, False),
+    ("c3_prec_1d", {}, True),
+    ("c2_hm_1d", {"tdi_gen": 15, "orbit": 0}, False),
+    ("c2_hm_1d", {"tdi_nested": 1}, False),
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name,over,prec", CASES)
+def test_node_differences_match_oracle(name, over, prec, precision):
+    rng = np.random.default_rng(11)
+    s, lk = _setup_pair(name, precision, 8, **over)
+    th0 = _theta0(prec, 0.75 * DAY)
+    nodes = wl.heterodyne_nodes(s.n, s.dt, th0[0], th0[1], th0[14])
+    lk.het_setup(th0, nodes)
+    walkers = _walkers(th0, rng, 6)
+    got = lk.het_deltas(_gpu(walkers)).cpu().numpy()
+    assert np.all(got[:, :, :, 0] == 0)                # the fiducial: dZ = 0 exactly
+    worst = _compare_deltas(got, s, walkers, th0, nodes, FP64_BAR if precision == 0 else MIXED_BAR)
+    print(f"{name} {over} precision {precision}: worst node difference {worst:.2e}")
+    lk.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("prec", [False, True])
+def test_model_and_loglike_match_oracle(prec, precision):
+    rng = np.random.default_rng(5)
+    name = "c3_prec_1d" if prec else "c2_hm_1d"
+    s, lk = _setup_pair(name, precision, 4)
+    th0 = _theta0(prec, 0.75 * DAY)
+    nodes = wl.heterodyne_nodes(s.n, s.dt, th0[0], th0[1], th0[14])
+    x0 = H.continuous_aet(th0, s)
+    data = x0                                  # zero-noise injection at the fiducial
+    lk.set_data(_gpu(data))
+    lk.het_setup(th0, nodes)
+    walkers = _walkers(th0, rng, 4)
+    model = lk.het_aet(_gpu(walkers)).double().cpu().numpy()
+    logl = lk.het_loglike(_gpu(walkers)).cpu().numpy()
+    for w, th in enumerate(walkers):
+        ref = H.model_aet(th, th0, s, nodes, x0)
+        scale = np.max(np.abs(ref))
+        e = np.max(np.abs(model[:, :, w] - ref)) / scale
+        assert e <= (1e-9 if precision == 0 else MIXED_BAR), (w, e)
+        ll = likelihood.loglike(ref, data, s.dt, s.f_lo, s.f_hi, s.tdi_gen, s.channel_mask)
+        # the T channel's low-frequency weight (S_T ~ f^6) amplifies the ~1e-11
+        # FP64 gap of the two responses (measured 1.6e-5 absolute, 8e-9 relative),
+        # and the mixed path's FP32 expansion (measured 5e-6 relative)
+        bar = max(1e-4, 2e-8 * abs(ll)) if precision == 0 else max(0.05, 1e-5 * abs(ll))
+        assert abs(logl[w] - ll) <= bar, (w, logl[w], ll)
+    lk.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_a_node_at_every_sample_is_the_continuous_response(precision):
+    """Small grid (n = 4320), every sample a node: the GPU model is the oracle's
+    continuous-time response of each walker."""
+    rng = np.random.default_rng(2)
+    s, lk = _setup_pair("c2_hm_1d", precision, 4, n=4320)
+    th0 = _theta0(False, 0.2 * DAY)
+    lk.het_setup(th0, np.arange(s.n))
+    walkers = _walkers(th0, rng, 3)
+    model = lk.het_aet(_gpu(walkers)).double().cpu().numpy()
+    for w, th in enumerate(walkers):
+        ref = H.continuous_aet(th, s)
+        e = np.max(np.abs(model[:, :, w] - ref)) / np.max(np.abs(ref))
+        assert e <= (1e-9 if precision == 0 else MIXED_BAR), (w, e)
+    lk.close()
+
+
+def test_fiducial_loglike_is_the_full_continuous_likelihood():
+    """logL at theta0 is the likelihood of X0 itself (dZ = 0): against the
+    oracle's continuous-time response of theta0.  The ~1e-11 FP64 gap of the
+    two responses is weighted by the T channel's PSD (S_T ~ f^6 at low f):
+    measured 3e-8 of logL, bar 2e-7."""
+    s, lk = _setup_pair("c2_hm_1d", 0, 1)
+    th0 = _theta0(False, 0.75 * DAY)
+    x0 = H.continuous_aet(th0, s)
+    data = 0.98 * x0
+    lk.set_data(_gpu(data))
+    lk.het_setup(th0, wl.heterodyne_nodes(s.n, s.dt, th0[0], th0[1], th0[14]))
+    got = float(lk.het_loglike(_gpu(th0[None, :]))[0])
+    ref = likelihood.loglike(x0, data, s.dt, s.f_lo, s.f_hi, s.tdi_gen)
+    assert abs(got - ref) <= 2e-7 * abs(ref)
+    lk.close()
+
+
+def test_setup_rejects_bad_nodes():
+    from paper_2501_08261_gb300 import api
+    s, lk = _setup_pair("c2_hm_1d", 1, 2, n=4320)
+    th0 = _theta0(False, 0.2 * DAY)
+    for bad in (np.array([0, 10]), np.array([1, s.n - 1]), np.array([0, 5, 5, s.n - 1]),
+                np.array([0])):
+        with pytest.raises(api.LisaTdError):
+            lk.het_setup(th0, bad)
+    q = th0.copy()
+    q[8] = -1.0
+    with pytest.raises(api.LisaTdError):
+        lk.het_setup(q, np.arange(s.n))
+    with pytest.raises(api.LisaTdError):            # no set-up yet
+        lk.het_loglike(_gpu(th0[None, :]))
+    lk.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sixty_days_sampled_nodes(precision):
+    """The 60-day, 5-mode, Keplerian TDI-2 grid at 64 walkers: node differences
+    of sampled nodes against the oracle, and logL finite with dZ = 0 at theta0."""
+    rng = np.random.default_rng(9)
+    s, lk = _setup_pair("c2_hm_60d", precision, 64)
+    th0 = _theta0(False, 55.0 * DAY)
+    nodes = wl.heterodyne_nodes(s.n, s.dt, th0[0], th0[1], th0[14])
+    lk.het_setup(th0, nodes)
+    walkers = _walkers(th0, rng, 64)
+    got = lk.het_deltas(_gpu(walkers)).cpu().numpy()
+    assert np.all(got[:, :, :, 0] == 0)
+    pick = np.unique(np.r_[0, rng.integers(0, nodes.size, 40), np.argmin(np.abs(nodes * s.dt - th0[14])),
+                           nodes.size - 1])
+    sub = got[pick][:, :, :, [0, 1, 2, 62, 63]]
+    worst = _compare_deltas(sub, s, walkers[[0, 1, 2, 62, 63]], th0, nodes[pick],
+                            FP64_BAR if precision == 0 else MIXED_BAR)
+    print(f"60 d precision {precision}: B = {nodes.size}, worst sampled node difference {worst:.2e}")
+    lk.set_data(torch.zeros((3, s.n), dtype=torch.float64, device="cuda"))
+    ll = lk.het_loglike(_gpu(walkers)).cpu().numpy()
+    assert np.all(np.isfinite(ll))
+    lk.close()
