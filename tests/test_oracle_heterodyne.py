@@ -190,10 +190,13 @@ def test_node_rule_shape():
     nodes = wl.heterodyne_nodes(n, dt, th0[0], th0[1], 50.0 * DAY)
     d = np.diff(nodes)
     assert nodes[0] == 0 and nodes[-1] == n - 1 and np.all(d >= 1)
-    assert np.max(d) <= 3600.0 / dt
+    assert np.max(d) <= 14400.0 / dt
     assert len(nodes) < 10000
     # every sample across the merger, sky delay included
     tc_i = int(50.0 * DAY / dt)
     assert np.all(d[(nodes[:-1] > tc_i - 104) & (nodes[:-1] < tc_i + 104)] == 1)
+    # every 250 s over the start taper (the signal starts before the grid here)
+    first = nodes[nodes * dt <= 1.0e4]
+    assert first[0] == 0 and np.max(np.diff(first)) <= 50
     small = wl.heterodyne_nodes(100, dt, th0[0], th0[1], 1e9)
     assert small[0] == 0 and small[-1] == 99
