@@ -264,8 +264,13 @@ int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_de
  * lisa_td_het_setup: fiducial theta0_host [15] (host), nodes_host [B] (host,
  * int64 sample indices rising strictly from 0 to n - 1, B >= 2).  Computes
  * the fiducial's carriers, X0 and node values; replaces an earlier set-up.
- * Allocates about n (3 x 28 + nmodes x 24) + B x (48 x 160 + nmodes x 24 x
- * (max_walkers + 1)) bytes; synchronises `stream`.  LISA_TD_EINVAL for NULL
+ * Allocates n (76 + 24 nmodes) + 96 x 48 x max(B, 16384) + 48 nmodes B
+ * + 3 nmodes B (16 or 8) max_walkers bytes (48 = the TDI-2 terms of X, Y, Z,
+ * 24 for TDI 1.5; the last term is the node differences, 16 B per complex
+ * value in FP64 contexts, 8 in mixed ones); synchronises `stream`.  The node
+ * sums are FP64 in both precisions (FP32 terms would leave rounding that the
+ * TDI combinations do not cancel); a mixed context rounds each node
+ * difference to FP32 and expands and transforms in FP32.  LISA_TD_EINVAL for NULL
  * pointers, bad nodes or an invalid fiducial (the prep checks of
  * lisa_td_loglike_batch), LISA_TD_ENOMEM, LISA_TD_ECUDA.  Every orbit kind,
  * TDI generation and delay form of the context is supported; ragged batches
