@@ -282,8 +282,51 @@ __device__ inline void ylmd_pair(const QPowD& P, const HetMode& D, double& ypr, 
   ylmd_pow<L, -M>(P, D.yc[1], ymr, ymi);
 }
 
-// absolute time t; zero outside [t0, t_end]
-template <bool PREC>
+// FP64 roots and reciprocals from an FP32 seed refined by two Newton steps
+// whose slope is kept from the seed: each step multiplies the relative error
+// by ~1e-7 (plus the quadratic term), so the results land at FP64 rounding
+// (one step leaves ~1e-14: random per evaluation, which the TDI sums do not
+// cancel) at a fraction of the FP64 pipe's cost of sqrt, cbrt and division
+__device__ __forceinline__ double rcp_nr(double a) {          // 1 / a, a > 0 normal
+  double r = (double)__frcp_rn((float)a);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) r = fma(r, fma(-a, r, 1.0), r);
+  return r;
+}
+__device__ __forceinline__ double root8_nr(double x) {        // x^(1/8), x > 0
+  const float xf = (float)x;
+  const float uf = sqrtf(sqrtf(sqrtf(xf)));
+  const double slope = (double)(uf / (8.0f * xf));            // 1 / (8 u^7) = u / (8 x)
+  double u = (double)uf;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double u2 = u * u, u4 = u2 * u2;
+    u = fma(x - u4 * u4, slope, u);
+  }
+  return u;
+}
+__device__ __forceinline__ double cbrt_nr(double a) {         // a^(1/3), a > 0
+  const float vf = cbrtf((float)a);
+  const double slope = (double)(1.0f / (3.0f * vf * vf));
+  double v = (double)vf;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) v = fma(a - v * v * v, slope, v);
+  return v;
+}
+
+// x - 2 pi k with k = rint(x / 2 pi): |result| <= pi, for the phases of
+// months-long chirps (up to ~1e6 rad); 2 pi split into its double and the
+// double of the remainder (2 pi - 6.283185307179586 = 2.449293598294706e-16)
+__device__ __forceinline__ double reduce_2pi(double x) {
+  const double k = rint(x * 0.15915494309189535);
+  const double r = fma(-k, 6.283185307179586, x);
+  return fma(-k, 2.4492935982947064e-16, r);
+}
+
+// absolute time t; zero outside [t0, t_end].  RAW (aligned spins only):
+// acc[j] += ap h_j, the angular weights left to the caller, which applies them
+// once to the difference of a link's two ends
+template <bool PREC, bool RAW = false>
 __device__ __forceinline__ void modes_fp64(const HetWalker& H, const WalkerRec& W, double t,
                                            double t0, double t_end, double ap, double ax,
                                            double2 (&acc)[kNMode]) {
@@ -293,17 +336,17 @@ __device__ __forceinline__ void modes_fp64(const HetWalker& H, const WalkerRec& 
   const bool insp = t < H.tm;
   double u = W.um, Mw = 0.0, tau = 0.0, dec = 1.0, e1r = 1.0, e1i = 0.0, v = 0.0;
   if (insp) {
-    u = sqrt(sqrt(sqrt(H.kap * (H.tc - t))));
-    const double iu = 1.0 / u;
+    u = root8_nr(H.kap * (H.tc - t));
+    const double iu = rcp_nr(u);
     const double iu2 = iu * iu, iu3 = iu2 * iu;
     Mw = 0.125 * (iu3 + H.c1 * iu2 * iu3 + H.cs * iu3 * iu3);        // M omega
     const double u2 = u * u;
     const double ph = -(u2 * u2 * u + (5.0 / 3.0) * H.c1 * u2 * u + 2.5 * H.cs * u2) * H.invnu;
     double s1, c1;
-    sincos(ph, &s1, &c1);
+    sincos(reduce_2pi(ph), &s1, &c1);
     e1r = c1;                                    // e^{-i phi}
     e1i = -s1;
-    v = cbrt(Mw);
+    v = cbrt_nr(Mw);
   } else {
     tau = t - H.tm;
     dec = exp(-tau / H.tau_d);
@@ -357,6 +400,12 @@ __device__ __forceinline__ void modes_fp64(const HetWalker& H, const WalkerRec& 
     const double f = freq * (0.5 / kPi);
     amp *= f > kFhi1 ? win * planck_down_f(f) : win;
     if (amp == 0.0) continue;
+    if (RAW) {
+      const double a = ap * amp;
+      acc[j].x = fma(a, hr, acc[j].x);
+      acc[j].y = fma(a, hi, acc[j].y);
+      continue;
+    }
     double ppr, ppi, pxr, pxi;
     if (PREC) {
       double ypr, ypi, ymr, ymi;
@@ -437,13 +486,27 @@ __global__ void __launch_bounds__(kNodeThreads) het_nodes_kernel(
     const double ks = k0 * G.rs[0] + k1 * G.rs[1] + k2 * G.rs[2];
     const double kn = k0 * G.n[0] + k1 * G.n[1] + k2 * G.n[2];
     const double un = dot3(W.u, G.n), vn = dot3(W.v, G.n);
-    const double den = G.sign / (2.0 * (1.0 - kn));
+    const double den = 0.5 * G.sign * rcp_nr(1.0 - kn);
     const double ap = den * (un * un - vn * vn), axx = den * 2.0 * un * vn;
     double2 tmp[kNMode];
 #pragma unroll
     for (int j = 0; j < kNMode; ++j) tmp[j] = make_double2(0.0, 0.0);
-    modes_fp64<PREC>(H, W, G.tp - G.L - ks, t0, t_end, ap, axx, tmp);
-    modes_fp64<PREC>(H, W, G.tp - kr, t0, t_end, -ap, -axx, tmp);
+    if (PREC) {
+      modes_fp64<PREC>(H, W, G.tp - G.L - ks, t0, t_end, ap, axx, tmp);
+      modes_fp64<PREC>(H, W, G.tp - kr, t0, t_end, -ap, -axx, tmp);
+    } else {
+      // constant angular weights: h(t_s) - h(t_r) first, weighted once
+      modes_fp64<PREC, true>(H, W, G.tp - G.L - ks, t0, t_end, 1.0, 0.0, tmp);
+      modes_fp64<PREC, true>(H, W, G.tp - kr, t0, t_end, -1.0, 0.0, tmp);
+#pragma unroll
+      for (int j = 0; j < kNMode; ++j) {
+        if (j >= H.nmode) continue;
+        const HetMode& D = H.mode[j];
+        const double wr = ap * D.ppr + axx * D.pxr, wi = ap * D.ppi + axx * D.pxi;
+        const double hr = tmp[j].x, hi = tmp[j].y;
+        tmp[j] = make_double2(hr * wr - hi * wi, hr * wi + hi * wr);
+      }
+    }
     add_channel(q / ntc, tmp, ax, ay, az);
   }
   const int64_t ib = nodes ? nodes[b] : start + b;
@@ -503,7 +566,9 @@ __global__ void __launch_bounds__(256) het_expand_kernel(
     const int b = bin[i];
     if (b != cur) {
       cur = b;
-      const int64_t na = nodes[b], nb = nodes[b + 1];
+      // 32-bit sample indices (n < 2^24): a 64-bit integer conversion would
+      // run on the FP64 pipe
+      const int na = (int)nodes[b], nb = (int)nodes[b + 1];
       ib = (R)na;
       inv = R(1) / (R)(nb - na);
 #pragma unroll
@@ -517,7 +582,7 @@ __global__ void __launch_bounds__(256) het_expand_kernel(
           dd[j][c].y = e.y - a.y;
         }
     }
-    const R s = ((R)i - ib) * inv;
+    const R s = ((R)(int)i - ib) * inv;
     C2 cj[NM];
 #pragma unroll
     for (int j = 0; j < NM; ++j) cj[j] = car[i * NM + j];
