@@ -175,6 +175,7 @@ struct HetMode {
 };
 struct HetWalker {
   double kap, invnu, invM, c1, cs, tc, tm, t_start, t_a, tau_d, c2psi, s2psi;
+  double mw_taper;                         // M omega at which the highest m reaches kFhi1
   int status, nmode;
   HetMode mode[kNMode];
 };
@@ -194,6 +195,9 @@ __device__ void het_walker_fill(const WalkerRec& W, HetWalker& H) {
   H.s2psi = W.s2psi;
   H.status = W.status;
   H.nmode = W.nmode;
+  int mmax = 1;
+  for (int j = 0; j < W.nmode; ++j) mmax = W.mode[j].m > mmax ? W.mode[j].m : mmax;
+  H.mw_taper = 2.0 * kPi * kFhi1 * W.M / mmax;
   for (int j = 0; j < W.nmode; ++j) {
     const ModeRec& Md = W.mode[j];
     HetMode& D = H.mode[j];
@@ -351,6 +355,37 @@ __device__ __forceinline__ void modes_fp64(const HetWalker& H, const WalkerRec& 
     tau = t - H.tm;
     dec = exp(-tau / H.tau_d);
   }
+  if (RAW && insp) {
+    // acc[j] += ap A_j e^{-i m_j phi}: one multiply and two FMAs per mode; the
+    // high-frequency taper is looked at only once some mode can reach it
+    const bool taper = Mw > H.mw_taper;
+    const double v2 = v * v;
+    const double w0 = ap * win * v2, w1 = w0 * v, w2 = w1 * v;
+    double pr[5], pim[5];
+    pr[1] = e1r; pim[1] = e1i;
+#pragma unroll
+    for (int m = 2; m <= 4; ++m) {
+      pr[m] = pr[m - 1] * e1r - pim[m - 1] * e1i;
+      pim[m] = pr[m - 1] * e1i + pim[m - 1] * e1r;
+    }
+#pragma unroll
+    for (int j = 0; j < kNMode; ++j) {
+      if (j >= H.nmode) continue;
+      const HetMode& D = H.mode[j];
+      double a = D.pref * (D.pw == 0 ? w0 : (D.pw == 1 ? w1 : w2));
+      if (taper) a *= planck_down_f(D.m * Mw * H.invM * (0.5 / kPi));
+      double hr = pr[1], hi = pim[1];
+#pragma unroll
+      for (int k = 2; k <= 4; ++k)
+        if (k == D.m) {
+          hr = pr[k];
+          hi = pim[k];
+        }
+      acc[j].x = fma(a, hr, acc[j].x);
+      acc[j].y = fma(a, hi, acc[j].y);
+    }
+    return;
+  }
   QPowD P;
   if (PREC) {
     double cbh, sbh, al, ga;
@@ -479,35 +514,54 @@ __global__ void __launch_bounds__(kNodeThreads) het_nodes_kernel(
 #pragma unroll
   for (int j = 0; j < kNMode; ++j) ax[j] = ay[j] = az[j] = make_double2(0.0, 0.0);
   const double k0 = W.k[0], k1 = W.k[1], k2 = W.k[2];
+  // aligned spins: per channel, S1_j = sum_terms ap dh_j and S2_j = sum_terms ax dh_j
+  // (dh = h(t_s) - h(t_r)); the constant angular weights are applied once per
+  // channel: X_j = (P + sg conj Q)_j S1_j + i (P - sg conj Q)_j S2_j
+  double2 s1[kNMode], s2[kNMode];
+#pragma unroll
+  for (int j = 0; j < kNMode; ++j) s1[j] = s2[j] = make_double2(0.0, 0.0);
   for (int q = 0; q < 3 * ntc; ++q) {
     const HetGeom64 G = g[(int64_t)q * B + b];
-    if (G.sign == 0.0) continue;
-    const double kr = k0 * G.rr[0] + k1 * G.rr[1] + k2 * G.rr[2];
-    const double ks = k0 * G.rs[0] + k1 * G.rs[1] + k2 * G.rs[2];
-    const double kn = k0 * G.n[0] + k1 * G.n[1] + k2 * G.n[2];
-    const double un = dot3(W.u, G.n), vn = dot3(W.v, G.n);
-    const double den = 0.5 * G.sign * rcp_nr(1.0 - kn);
-    const double ap = den * (un * un - vn * vn), axx = den * 2.0 * un * vn;
-    double2 tmp[kNMode];
+    if (G.sign != 0.0) {
+      const double kr = k0 * G.rr[0] + k1 * G.rr[1] + k2 * G.rr[2];
+      const double ks = k0 * G.rs[0] + k1 * G.rs[1] + k2 * G.rs[2];
+      const double kn = k0 * G.n[0] + k1 * G.n[1] + k2 * G.n[2];
+      const double un = dot3(W.u, G.n), vn = dot3(W.v, G.n);
+      const double den = 0.5 * G.sign * rcp_nr(1.0 - kn);
+      const double ap = den * (un * un - vn * vn), axx = den * 2.0 * un * vn;
+      double2 tmp[kNMode];
 #pragma unroll
-    for (int j = 0; j < kNMode; ++j) tmp[j] = make_double2(0.0, 0.0);
-    if (PREC) {
-      modes_fp64<PREC>(H, W, G.tp - G.L - ks, t0, t_end, ap, axx, tmp);
-      modes_fp64<PREC>(H, W, G.tp - kr, t0, t_end, -ap, -axx, tmp);
-    } else {
-      // constant angular weights: h(t_s) - h(t_r) first, weighted once
-      modes_fp64<PREC, true>(H, W, G.tp - G.L - ks, t0, t_end, 1.0, 0.0, tmp);
-      modes_fp64<PREC, true>(H, W, G.tp - kr, t0, t_end, -1.0, 0.0, tmp);
+      for (int j = 0; j < kNMode; ++j) tmp[j] = make_double2(0.0, 0.0);
+      if (PREC) {
+        modes_fp64<PREC>(H, W, G.tp - G.L - ks, t0, t_end, ap, axx, tmp);
+        modes_fp64<PREC>(H, W, G.tp - kr, t0, t_end, -ap, -axx, tmp);
+        add_channel(q / ntc, tmp, ax, ay, az);
+      } else {
+        modes_fp64<PREC, true>(H, W, G.tp - G.L - ks, t0, t_end, 1.0, 0.0, tmp);
+        modes_fp64<PREC, true>(H, W, G.tp - kr, t0, t_end, -1.0, 0.0, tmp);
 #pragma unroll
-      for (int j = 0; j < kNMode; ++j) {
-        if (j >= H.nmode) continue;
-        const HetMode& D = H.mode[j];
-        const double wr = ap * D.ppr + axx * D.pxr, wi = ap * D.ppi + axx * D.pxi;
-        const double hr = tmp[j].x, hi = tmp[j].y;
-        tmp[j] = make_double2(hr * wr - hi * wi, hr * wi + hi * wr);
+        for (int j = 0; j < kNMode; ++j) {
+          s1[j].x = fma(ap, tmp[j].x, s1[j].x);
+          s1[j].y = fma(ap, tmp[j].y, s1[j].y);
+          s2[j].x = fma(axx, tmp[j].x, s2[j].x);
+          s2[j].y = fma(axx, tmp[j].y, s2[j].y);
+        }
       }
     }
-    add_channel(q / ntc, tmp, ax, ay, az);
+    if (!PREC && (q + 1) % ntc == 0) {             // end of channel q / ntc
+      double2 t2[kNMode];
+#pragma unroll
+      for (int j = 0; j < kNMode; ++j) {
+        t2[j] = make_double2(0.0, 0.0);
+        if (j < H.nmode) {
+          const HetMode& D = H.mode[j];
+          t2[j].x = D.ppr * s1[j].x - D.ppi * s1[j].y + D.pxr * s2[j].x - D.pxi * s2[j].y;
+          t2[j].y = D.ppr * s1[j].y + D.ppi * s1[j].x + D.pxr * s2[j].y + D.pxi * s2[j].x;
+        }
+        s1[j] = s2[j] = make_double2(0.0, 0.0);
+      }
+      add_channel(q / ntc, t2, ax, ay, az);
+    }
   }
   const int64_t ib = nodes ? nodes[b] : start + b;
   const int nm = H.nmode;
