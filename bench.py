@@ -360,6 +360,16 @@ def heterodyne_measure(torch, api, workloads, kw, cfg, params, nball, steps):
                                  "fft_pass2_norm": st["fft_pass2_norm"] / calls,
                                  "reduce": st["reduce"] / calls})
         lk.close()
+    # the node rule's own error at this size: against the same likelihood with
+    # a node at every sample (the continuous-time likelihood itself), FP64, on
+    # the injection and the first Fisher-ball walkers
+    nsub = min(W, 1 + min(nball, 7))
+    lkf = api.Likelihood(precision=0, max_walkers=nsub, **kw)
+    lkf.het_setup(th0, np.arange(cfg["n"], dtype=np.int64))
+    lkf.set_data(data)
+    lfull = lkf.het_loglike(params[:nsub]).cpu().numpy()
+    lkf.close()
+    rule_err = np.abs(res[0]["logl"][:nsub] - lfull)
     d = np.abs(res[1]["logl"] - res[0]["logl"])
     ball = slice(0, 1 + nball)
     l64 = res[0]["logl"]
@@ -377,6 +387,11 @@ def heterodyne_measure(torch, api, workloads, kw, cfg, params, nball, steps):
                                                               float(l64[ball].max())],
                               "max_rel_dlogL_far": (float((d[far] / np.abs(l64[far])).max())
                                                     if far.any() else None)},
+            "node_rule_error": {"walkers": nsub,
+                                "max_abs_dlogL_vs_every_sample": float(rule_err.max()),
+                                "logL_range": [float(lfull.min()), float(lfull.max())],
+                                "note": "FP64, the same likelihood with a node at every sample "
+                                        "(the continuous-time response) as the reference"},
             "definition": "fiducial = the injection; nodes: every sample across the merger, "
                           "chirp-rate spacing (df 5e-6 Hz, <= 4 h) elsewhere, 250 s over the start "
                           "taper; node sums FP64, expansion + FFT FP32; data = the fiducial's "

@@ -210,3 +210,34 @@ def test_sixty_days_sampled_nodes(precision):
     ll = lk.het_loglike(_gpu(walkers)).cpu().numpy()
     assert np.all(np.isfinite(ll))
     lk.close()
+
+
+def test_node_rule_error_at_sixty_days():
+    """The default node rule against a node at every sample (the continuous-time
+    likelihood itself) on the 60-day grid, FP64: the rule's own approximation
+    error at full size, from walkers at the posterior's scale to far ones."""
+    from paper_2501_08261_gb300 import api
+    cfg = wl.config("c2_hm_60d")
+    th0 = _theta0(False, 55.0 * DAY)
+    # rows: the fiducial, two walkers at a tenth of the one-day widths (logL ~ -30
+    # at 60 d), one at the full widths (logL ~ -3e3), two at thirty widths
+    base = _walkers(th0, np.random.default_rng(21), 6)
+    walkers = np.concatenate([base[:1], th0 + 0.1 * (base[1:3] - th0), base[3:4], base[4:]])
+    nodes = wl.heterodyne_nodes(cfg["n"], cfg["dt"], th0[0], th0[1], th0[14])
+    full = api.Likelihood(precision=0, max_walkers=6, **cfg)
+    full.het_setup(th0, np.arange(cfg["n"], dtype=np.int64))
+    data = full.het_aet(_gpu(th0[None, :]))[:, :, 0].contiguous()
+    full.set_data(data)
+    ref = full.het_loglike(_gpu(walkers)).cpu().numpy()
+    full.close()
+    lk = api.Likelihood(precision=0, max_walkers=6, **cfg)
+    lk.het_setup(th0, nodes)
+    lk.set_data(data)
+    got = lk.het_loglike(_gpu(walkers)).cpu().numpy()
+    lk.close()
+    d = np.abs(got - ref)
+    print(f"60 d node rule (B = {nodes.size}): logL {ref}, |d| {d}")
+    assert d[0] <= 1e-9 * max(1.0, abs(ref[0]))
+    assert np.all(d[1:3] <= 0.02), d                 # posterior scale
+    assert d[3] <= 1.0, d                            # measured 0.20 at logL -3.3e3
+    assert np.all(d[4:] <= 1e-4 * np.abs(ref[4:])), d   # measured 1e-5 .. 4e-5
