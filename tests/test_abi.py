@@ -63,6 +63,12 @@ def test_argument_errors_need_no_gpu(libpath):
     assert lib.lisa_td_create(ctypes.byref(h), ctypes.byref(bad), None) == -1
     assert lib.lisa_td_create(None, ctypes.byref(bad), None) == -1
     assert lib.lisa_td_loglike_batch(None, None, 1, None, None, None) == -1
+    # heterodyned likelihood: NULL context / arguments are refused before any device work
+    assert lib.lisa_td_het_setup(None, None, None, 2, None) == -1
+    assert b"NULL" in lib.lisa_td_last_error()
+    assert lib.lisa_td_het_loglike(None, None, 1, None, None, None) == -1
+    assert lib.lisa_td_het_deltas(None, None, 1, None, None) == -1
+    assert lib.lisa_td_het_aet(None, None, 1, None, None) == -1
 
 
 def test_missing_library_fails_loudly(tmp_path):
