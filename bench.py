@@ -393,8 +393,8 @@ def heterodyne_measure(torch, api, workloads, kw, cfg, params, nball, steps):
                                 "note": "FP64, the same likelihood with a node at every sample "
                                         "(the continuous-time response) as the reference"},
             "definition": "fiducial = the injection; nodes: every sample across the merger, "
-                          "chirp-rate spacing (df 5e-6 Hz, <= 4 h) elsewhere, 250 s over the start "
-                          "taper; node sums FP64, expansion + FFT FP32; data = the fiducial's "
+                          "chirp-rate spacing (df 2e-5 Hz, <= 12 h) elsewhere, 250 s over the start "
+                          "taper; cubic interpolation between nodes; node sums FP64, expansion + FFT FP32; data = the fiducial's "
                           "continuous-time response"}
 
 

@@ -253,7 +253,10 @@ int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_de
  *   - with a fiducial theta0, carriers C_j(t) = e^{-i Phi_lm(t; theta0)} and
  *     nodes 0 = i_0 < ... < i_{B-1} = n - 1, the node differences are
  *     dZ_jc,b = conj(C_j(t_b)) (X_jc(t_b; theta) - X_jc(t_b; theta0));
- *   - the model on the grid is X0_c(t_i) + Re sum_j C_j(t_i) lerp_b(dZ_jc)(t_i),
+ *   - the model on the grid is X0_c(t_i) + Re sum_j C_j(t_i) P_jc(i), P_jc the
+ *     cubic Lagrange polynomial through the node differences of the nodes
+ *     a .. a + 3 around sample i (a = min(max(b - 1, 0), B - 4), b the node
+ *     interval holding i),
  *     X0 = Re sum_j X_jc(t_i; theta0) (computed once in FP64), and logL is the
  *     full likelihood's DFT + PSD-weighted norm of model - data.
  * At theta0 the model is X0 exactly; with a node at every sample it is the
@@ -262,7 +265,7 @@ int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_de
  * complex multiply-add per mode and channel.
  *
  * lisa_td_het_setup: fiducial theta0_host [15] (host), nodes_host [B] (host,
- * int64 sample indices rising strictly from 0 to n - 1, B >= 2).  Computes
+ * int64 sample indices rising strictly from 0 to n - 1, B >= 4).  Computes
  * the fiducial's carriers, X0 and node values; replaces an earlier set-up.
  * Allocates n (76 + 24 nmodes) + 96 x 48 x max(B, 16384) + 48 nmodes B
  * + 3 nmodes B (16 or 8) max_walkers bytes (48 = the TDI-2 terms of X, Y, Z,

@@ -29,8 +29,11 @@ indices 0 = i_0 < i_1 < ... < i_{B-1} = n - 1.
 3. Carriers.  C_j(t) = e^{-i Phi_lm(t; theta0)}, the fiducial's own mode phase.
 4. Node differences.  dZ_jc,b = conj(C_j(t_b)) [X_jc(t_b; theta) - X_jc(t_b; theta0)]
    at the nodes t_b = t0 + i_b dt: slowly varying where theta is near theta0.
-5. Model.  For i_b <= i <= i_{b+1}, s = (i - i_b) / (i_{b+1} - i_b):
-       h_c(t_i) = X0_c(t_i) + Re sum_j C_j(t_i) ((1 - s) dZ_jc,b + s dZ_jc,b+1),
+5. Model.  For i_b <= i < i_{b+1} (B >= 4 nodes), the cubic Lagrange polynomial
+   through the four nodes a .. a + 3, a = min(max(b - 1, 0), B - 4) (the
+   stencil moved inwards at the ends):
+       h_c(t_i) = X0_c(t_i) + Re sum_j C_j(t_i) sum_q w_q(i) dZ_jc,a+q,
+       w_q(i) = prod_{r != q} (i - i_{a+r}) / (i_{a+q} - i_{a+r}),
    X0_c = Re sum_j X_jc(t_i; theta0), the fiducial's continuous-time response
    on the grid.  At theta = theta0 every dZ is 0 and the model is X0; with a
    node at every sample it is Re sum_j X_jc(t_i; theta), the continuous-time
@@ -138,16 +141,23 @@ def node_deltas(theta, theta0, s: pipeline.Setup, node_idx):
 def expand(dz, theta0, s: pipeline.Setup, node_idx, x0):
     """The model A, E, T on the grid (step 5) from node differences dz."""
     node_idx = np.asarray(node_idx, dtype=np.int64)
-    if node_idx[0] != 0 or node_idx[-1] != s.n - 1 or np.any(np.diff(node_idx) <= 0):
-        raise ValueError("nodes must rise strictly from 0 to n - 1")
+    B = node_idx.size
+    if B < 4 or node_idx[0] != 0 or node_idx[-1] != s.n - 1 or np.any(np.diff(node_idx) <= 0):
+        raise ValueError("nodes must be at least four, rising strictly from 0 to n - 1")
     i = np.arange(s.n)
-    b = np.clip(np.searchsorted(node_idx, i, side="right") - 1, 0, node_idx.size - 2)
-    sfrac = (i - node_idx[b]) / (node_idx[b + 1] - node_idx[b])
+    b = np.clip(np.searchsorted(node_idx, i, side="right") - 1, 0, B - 2)
+    a = np.clip(b - 1, 0, B - 4)
+    x = node_idx[a[:, None] + np.arange(4)].astype(np.float64)      # [n][4]
+    w = np.ones((s.n, 4))
+    for q in range(4):
+        for r in range(4):
+            if r != q:
+                w[:, q] *= (i - x[:, r]) / (x[:, q] - x[:, r])
     c = carriers(theta0, s, pipeline.grid(s))
     out = np.array(x0, dtype=np.float64, copy=True)
     for j in range(dz.shape[0]):
         for ch in range(3):
-            env = (1.0 - sfrac) * dz[j, ch, b] + sfrac * dz[j, ch, b + 1]
+            env = sum(w[:, q] * dz[j, ch, a + q] for q in range(4))
             out[ch] += (c[j] * env).real
     return out
 

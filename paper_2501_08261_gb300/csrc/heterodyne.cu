@@ -9,7 +9,7 @@
 //                 and reception times of Eq. (yslr) (two evaluations per term),
 //                 then A, E, T, the demodulation by the fiducial carrier and the
 //                 difference to the fiducial's own node value;
-//   expand kernel at every grid sample: X0 - d + Re sum_j C_j lerp(dZ_j) per
+//   expand kernel at every grid sample: X0 - d + Re sum_j C_j cubic(dZ_j) per
 //                 channel, written in the residual layout of the full path;
 // then the full path's FFT pass 1, pass 2 + PSD-weighted norm and reduction.
 // The walker-independent pieces -- the delayed times and link geometry of every
@@ -599,54 +599,81 @@ __global__ void __launch_bounds__(kNodeThreads) het_nodes_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// expansion: r[c][i][ldw] = base[c][i] + Re sum_j C_j(i) (dZ_b + s (dZ_b+1 - dZ_b))
-// lane = walker, each warp a run of `chunk` consecutive samples (the node pair
-// and its coefficients stay in registers while the bin does not change)
+// expansion: r[c][i][ldr] = base[c][i] + Re sum_j C_j(i) sum_q w_q(i) dZ_j,a+q,
+// the cubic Lagrange polynomial through the nodes a .. a + 3 around sample i
+// (a = min(max(b - 1, 0), B - 4), b the node interval holding i).  Lane =
+// walker; each warp a run of `chunk` consecutive samples, the four nodes'
+// values kept in registers while the interval does not change.
 // ---------------------------------------------------------------------------
 
+constexpr int kExpandWarps = 4;       // warps per block of the expansion
+constexpr int kExpandMinBlocks = 4;   // resident blocks per SM it is compiled for
+
 template <typename R, typename C2, int NM>
-__global__ void __launch_bounds__(256) het_expand_kernel(
+__global__ void __launch_bounds__(32 * kExpandWarps, kExpandMinBlocks) het_expand_kernel(
     int64_t n, int chunk, const int32_t* __restrict__ bin, const int64_t* __restrict__ nodes,
-    const C2* __restrict__ car, const R* __restrict__ base, const C2* __restrict__ dz,
+    int B, const C2* __restrict__ car, const R* __restrict__ base, const C2* __restrict__ dz,
     int ldz, R* __restrict__ r, int ldr, int W) {
   const int w = blockIdx.y * 32 + threadIdx.x;
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.y + threadIdx.y) * chunk;
   if (i0 >= n) return;
   const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
-  int cur = -1;
-  C2 z[NM][3], dd[NM][3];
-  R ib = R(0), inv = R(0);
-  for (int64_t i = i0; i < i1; ++i) {
-    const int b = bin[i];
-    if (b != cur) {
-      cur = b;
-      // 32-bit sample indices (n < 2^24): a 64-bit integer conversion would
-      // run on the FP64 pipe
-      const int na = (int)nodes[b], nb = (int)nodes[b + 1];
-      ib = (R)na;
-      inv = R(1) / (R)(nb - na);
+  // the cubic in Newton's form on the local variable s = (i - i_a1) / (i_a2 - i_a1)
+  // (nodes at s0 < 0, 0, 1, s3 > 1): f0 + (s - s0)(f01 + s (f012 + (s - 1) f0123)),
+  // coefficients O(|dZ|) whatever the node spacing, three complex FMAs per
+  // sample; one channel at a time, so that only its modes' coefficients
+  // occupy registers
+#pragma unroll 1
+  for (int c = 0; c < 3; ++c) {
+    int cur = -1;
+    C2 f[NM][4];
+    R xa1 = R(0), sc = R(0), s0 = R(0);
+    for (int64_t i = i0; i < i1; ++i) {
+      const int b = bin[i];
+      if (b != cur) {
+        cur = b;
+        int a = b - 1 < 0 ? 0 : b - 1;
+        a = a > B - 4 ? B - 4 : a;
+        // 32-bit sample indices (n < 2^24): a 64-bit integer conversion would
+        // run on the FP64 pipe
+        const R x0 = (R)(int)nodes[a], x1 = (R)(int)nodes[a + 1];
+        const R x2 = (R)(int)nodes[a + 2], x3 = (R)(int)nodes[a + 3];
+        xa1 = x1;
+        sc = R(1) / (x2 - x1);
+        s0 = (x0 - x1) * sc;
+        const R s3 = (x3 - x1) * sc;
+        const R i01 = R(1) / (R(0) - s0), i23 = R(1) / (s3 - R(1));
+        const R i02 = R(1) / (R(1) - s0), i13 = R(1) / s3, i03 = R(1) / (s3 - s0);
 #pragma unroll
-      for (int j = 0; j < NM; ++j)
+        for (int j = 0; j < NM; ++j) {
+          C2 z[4];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const C2 a = dz[(((int64_t)b * NM + j) * 3 + c) * ldz + w];
-          const C2 e = dz[(((int64_t)(b + 1) * NM + j) * 3 + c) * ldz + w];
-          z[j][c] = a;
-          dd[j][c].x = e.x - a.x;
-          dd[j][c].y = e.y - a.y;
+          for (int q = 0; q < 4; ++q) z[q] = dz[(((int64_t)(a + q) * NM + j) * 3 + c) * ldz + w];
+          C2 d01, d12, d23, d012, d123, d0123;
+          d01.x = (z[1].x - z[0].x) * i01;  d01.y = (z[1].y - z[0].y) * i01;
+          d12.x = z[2].x - z[1].x;          d12.y = z[2].y - z[1].y;
+          d23.x = (z[3].x - z[2].x) * i23;  d23.y = (z[3].y - z[2].y) * i23;
+          d012.x = (d12.x - d01.x) * i02;   d012.y = (d12.y - d01.y) * i02;
+          d123.x = (d23.x - d12.x) * i13;   d123.y = (d23.y - d12.y) * i13;
+          d0123.x = (d123.x - d012.x) * i03; d0123.y = (d123.y - d012.y) * i03;
+          f[j][0] = z[0];
+          f[j][1] = d01;
+          f[j][2] = d012;
+          f[j][3] = d0123;
         }
-    }
-    const R s = ((R)(int)i - ib) * inv;
-    C2 cj[NM];
-#pragma unroll
-    for (int j = 0; j < NM; ++j) cj[j] = car[i * NM + j];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
+      }
+      const R sv = ((R)(int)i - xa1) * sc;
+      const R e0 = sv - s0, e2 = sv - R(1);
       R acc = base[c * n + i];
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
-        const R er = z[j][c].x + s * dd[j][c].x, ei = z[j][c].y + s * dd[j][c].y;
-        acc += cj[j].x * er - cj[j].y * ei;
+        const C2 cj = car[i * NM + j];
+        R er = f[j][2].x + e2 * f[j][3].x, ei = f[j][2].y + e2 * f[j][3].y;
+        er = f[j][1].x + sv * er;
+        ei = f[j][1].y + sv * ei;
+        er = f[j][0].x + e0 * er;
+        ei = f[j][0].y + e0 * ei;
+        acc += cj.x * er - cj.y * ei;
       }
       if (w < W) r[(c * n + i) * ldr + w] = acc;
     }
@@ -750,11 +777,12 @@ cudaError_t launch_expand_t(const lisa_td_ctx* c, const HetState* h, const C2* c
                             const R* base, const C2* dz, int ldz, R* r, int ldr, int W, int Wgrid,
                             cudaStream_t s) {
   const int chunk = 128;
-  dim3 block(32, 8);
-  dim3 grid((unsigned)((c->n + 8 * chunk - 1) / (8 * chunk)), (unsigned)(Wgrid / 32));
+  dim3 block(32, kExpandWarps);
+  dim3 grid((unsigned)((c->n + kExpandWarps * chunk - 1) / (kExpandWarps * chunk)),
+            (unsigned)(Wgrid / 32));
 #define HET_EXPAND(NM)                                                                        \
-  het_expand_kernel<R, C2, NM><<<grid, block, 0, s>>>(c->n, chunk, h->bin, h->nodes, car, base, \
-                                                      dz, ldz, r, ldr, W)
+  het_expand_kernel<R, C2, NM><<<grid, block, 0, s>>>(c->n, chunk, h->bin, h->nodes,            \
+                                                      (int)h->B, car, base, dz, ldz, r, ldr, W)
   switch (h->nm) {
     case 1: HET_EXPAND(1); break;
     case 2: HET_EXPAND(2); break;
@@ -808,9 +836,9 @@ int lisa_td_het_setup(lisa_td_ctx* c, const double* theta0_host, const int64_t* 
   for (int k = 0; k < kNPar; ++k)
     if (!isfinite(theta0_host[k]))
       return report_error(LISA_TD_EINVAL, "lisa_td_het_setup: fiducial entry %d is not finite", k);
-  if (B < 2 || nodes_host[0] != 0 || nodes_host[B - 1] != c->n - 1)
+  if (B < 4 || nodes_host[0] != 0 || nodes_host[B - 1] != c->n - 1)
     return report_error(LISA_TD_EINVAL,
-                        "lisa_td_het_setup: nodes must hold at least 2 indices from 0 to n - 1");
+                        "lisa_td_het_setup: nodes must hold at least 4 indices from 0 to n - 1");
   for (int64_t b = 1; b < B; ++b)
     if (nodes_host[b] <= nodes_host[b - 1])
       return report_error(LISA_TD_EINVAL, "lisa_td_het_setup: nodes must rise strictly (index %lld)",

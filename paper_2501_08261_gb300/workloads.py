@@ -195,7 +195,7 @@ def standard_normals(w, dim, seed):
     return np.random.default_rng(seed).normal(size=(w, dim))
 
 
-def heterodyne_nodes(n, dt, m1, m2, tc, t0=0.0, df=5e-6, dt_max=14400.0, x_dense=6.0,
+def heterodyne_nodes(n, dt, m1, m2, tc, t0=0.0, df=2e-5, dt_max=43200.0, x_dense=6.0,
                      sky_pad=520.0, ring_m=200.0, f_start=1e-4, taper=1.0e4, taper_step=250.0):
     """Node indices of the heterodyned likelihood for a fiducial of masses m1, m2
     [Msun] and merger parameter tc [s] on an n-sample grid.

@@ -176,6 +176,7 @@ def test_setup_rejects_bad_nodes():
     s, lk = _setup_pair("c2_hm_1d", 1, 2, n=4320)
     th0 = _theta0(False, 0.2 * DAY)
     for bad in (np.array([0, 10]), np.array([1, s.n - 1]), np.array([0, 5, 5, s.n - 1]),
+                np.array([0, 5, s.n - 1]),
                 np.array([0])):
         with pytest.raises(api.LisaTdError):
             lk.het_setup(th0, bad)
