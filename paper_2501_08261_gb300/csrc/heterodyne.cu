@@ -618,16 +618,16 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandMinBlocks) het_expan
   const int64_t i0 = ((int64_t)blockIdx.x * blockDim.y + threadIdx.y) * chunk;
   if (i0 >= n) return;
   const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
-  // the cubic in Newton's form on the local variable s = (i - i_a1) / (i_a2 - i_a1)
-  // (nodes at s0 < 0, 0, 1, s3 > 1): f0 + (s - s0)(f01 + s (f012 + (s - 1) f0123)),
-  // coefficients O(|dZ|) whatever the node spacing, three complex FMAs per
-  // sample; one channel at a time, so that only its modes' coefficients
-  // occupy registers
+  // one channel at a time, so that only its modes' four node values occupy
+  // registers.  Lagrange form: the weights of a sample within its interval
+  // stay O(1), so FP32 rounding stays at ~1e-7 of the node values even where
+  // an envelope far from the fiducial's is not smooth (the Newton form's
+  // divided differences are not bounded there and lose more)
 #pragma unroll 1
   for (int c = 0; c < 3; ++c) {
     int cur = -1;
-    C2 f[NM][4];
-    R xa1 = R(0), sc = R(0), s0 = R(0);
+    C2 z[NM][4];
+    R xs[4], dinv[4];
     for (int64_t i = i0; i < i1; ++i) {
       const int b = bin[i];
       if (b != cur) {
@@ -636,43 +636,37 @@ __global__ void __launch_bounds__(32 * kExpandWarps, kExpandMinBlocks) het_expan
         a = a > B - 4 ? B - 4 : a;
         // 32-bit sample indices (n < 2^24): a 64-bit integer conversion would
         // run on the FP64 pipe
-        const R x0 = (R)(int)nodes[a], x1 = (R)(int)nodes[a + 1];
-        const R x2 = (R)(int)nodes[a + 2], x3 = (R)(int)nodes[a + 3];
-        xa1 = x1;
-        sc = R(1) / (x2 - x1);
-        s0 = (x0 - x1) * sc;
-        const R s3 = (x3 - x1) * sc;
-        const R i01 = R(1) / (R(0) - s0), i23 = R(1) / (s3 - R(1));
-        const R i02 = R(1) / (R(1) - s0), i13 = R(1) / s3, i03 = R(1) / (s3 - s0);
 #pragma unroll
-        for (int j = 0; j < NM; ++j) {
-          C2 z[4];
+        for (int q = 0; q < 4; ++q) xs[q] = (R)(int)nodes[a + q];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) z[q] = dz[(((int64_t)(a + q) * NM + j) * 3 + c) * ldz + w];
-          C2 d01, d12, d23, d012, d123, d0123;
-          d01.x = (z[1].x - z[0].x) * i01;  d01.y = (z[1].y - z[0].y) * i01;
-          d12.x = z[2].x - z[1].x;          d12.y = z[2].y - z[1].y;
-          d23.x = (z[3].x - z[2].x) * i23;  d23.y = (z[3].y - z[2].y) * i23;
-          d012.x = (d12.x - d01.x) * i02;   d012.y = (d12.y - d01.y) * i02;
-          d123.x = (d23.x - d12.x) * i13;   d123.y = (d23.y - d12.y) * i13;
-          d0123.x = (d123.x - d012.x) * i03; d0123.y = (d123.y - d012.y) * i03;
-          f[j][0] = z[0];
-          f[j][1] = d01;
-          f[j][2] = d012;
-          f[j][3] = d0123;
+        for (int q = 0; q < 4; ++q) {
+          R den = R(1);
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (t != q) den *= xs[q] - xs[t];
+          dinv[q] = R(1) / den;
         }
+#pragma unroll
+        for (int j = 0; j < NM; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            z[j][q] = dz[(((int64_t)(a + q) * NM + j) * 3 + c) * ldz + w];
       }
-      const R sv = ((R)(int)i - xa1) * sc;
-      const R e0 = sv - s0, e2 = sv - R(1);
+      const R xi = (R)(int)i;
+      const R e0 = xi - xs[0], e1 = xi - xs[1], e2 = xi - xs[2], e3 = xi - xs[3];
+      const R e01 = e0 * e1, e23 = e2 * e3;
+      const R wq[4] = {e1 * e23 * dinv[0], e0 * e23 * dinv[1], e01 * e3 * dinv[2],
+                       e01 * e2 * dinv[3]};
       R acc = base[c * n + i];
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
         const C2 cj = car[i * NM + j];
-        R er = f[j][2].x + e2 * f[j][3].x, ei = f[j][2].y + e2 * f[j][3].y;
-        er = f[j][1].x + sv * er;
-        ei = f[j][1].y + sv * ei;
-        er = f[j][0].x + e0 * er;
-        ei = f[j][0].y + e0 * ei;
+        R er = R(0), ei = R(0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          er += wq[q] * z[j][q].x;
+          ei += wq[q] * z[j][q].y;
+        }
         acc += cj.x * er - cj.y * ei;
       }
       if (w < W) r[(c * n + i) * ldr + w] = acc;
