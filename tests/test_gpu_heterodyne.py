@@ -242,3 +242,31 @@ def test_node_rule_error_at_sixty_days():
     assert np.all(d[1:3] <= 0.02), d                 # posterior scale
     assert d[3] <= 1.0, d                            # measured 0.20 at logL -3.3e3
     assert np.all(d[4:] <= 1e-4 * np.abs(ref[4:])), d   # measured 1e-5 .. 4e-5
+
+
+def test_node_differences_on_an_orbit_table_match_oracle():
+    """orbit_kind 2: the node geometry comes from the library's resampling of
+    the caller's spacecraft positions, the oracle reads the same table through
+    its own interpolation (FP64, one day, TDI 2)."""
+    import dataclasses
+    from oracle import orbits
+    from paper_2501_08261_gb300 import api
+    t0_tab, dt_tab = -2 * 3600.0, 3600.0
+    cfg = wl.config("c2_hm_1d", orbit=2)
+    rows = int((cfg["n"] * cfg["dt"] - t0_tab) // dt_tab) + 10
+    pos = wl.orbit_table_positions(t0_tab, dt_tab, rows, 3)
+    s = pipeline.Setup(dt=cfg["dt"], n=cfg["n"], t0=cfg["t0"], f_lo=cfg["f_lo"], f_hi=cfg["f_hi"],
+                       tdi_gen=cfg["tdi_gen"], channel_mask=cfg["channel_mask"],
+                       lagrange_order=cfg["lagrange_order"],
+                       orbit=orbits.OrbitTable(t0_tab, dt_tab, pos), mode_mask=cfg["mode_mask"],
+                       precessing=False)
+    lk = api.Likelihood(precision=0, max_walkers=4, orbit_table=(t0_tab, dt_tab, pos), **cfg)
+    th0 = _theta0(False, 0.75 * DAY)
+    nodes = wl.heterodyne_nodes(s.n, s.dt, th0[0], th0[1], th0[14])
+    lk.het_setup(th0, nodes)
+    walkers = _walkers(th0, np.random.default_rng(13), 4)
+    got = lk.het_deltas(_gpu(walkers)).cpu().numpy()
+    assert np.all(got[:, :, :, 0] == 0)
+    worst = _compare_deltas(got, s, walkers, th0, nodes, FP64_BAR)
+    print(f"orbit table: worst node difference {worst:.2e}")
+    lk.close()
