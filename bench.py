@@ -411,7 +411,7 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    cfg = workloads.config(args.workload)
+    cfg = workloads.config(args.workload, **({"n": args.n} if args.n else {}))
     kw = _gpu_kwargs(cfg)
     W = args.walkers
     theta = workloads.prior_draws(W, cfg["n"], cfg["dt"], seed=walker_seed(rank))
@@ -654,6 +654,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--walkers", type=int, default=WALKERS)
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid length instead of the workload's (e.g. 1054080: 61 d at 5 s)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--no-proposals", action="store_true",

@@ -51,7 +51,9 @@ typedef struct lisa_td_ctx lisa_td_ctx;   /* opaque */
 
 typedef struct {
   double  dt;              /* sample spacing [s] (Sec. II.C: 5 s)                 */
-  int64_t n;               /* samples per series, 2^a 3^b 5^c 7^d, 64..2^24       */
+  int64_t n;               /* samples per series, 64..2^24: 2^a 3^b 5^c 7^d times
+                            * at most one prime in [11, 127] (61 days at 5 s:
+                            * 2^7 3^3 5 61)                                      */
   double  t0;              /* time of sample 0 [s]                               */
   double  f_lo, f_hi;      /* inner-product band [Hz] (Sec. II.C)                */
   int32_t tdi_gen;         /* 15 (X_1.5) or 20 (X_2)                             */
@@ -157,7 +159,7 @@ int lisa_td_noise(lisa_td_ctx* ctx, const double* z_dev, double* noise_dev, void
  * t0 + (n - n_w + j) dt, j < n_w), with the data restricted to that window
  * and its own DFT of length n_w (frequency resolution 1 / (n_w dt)); the
  * result is what lisa_td_loglike_batch gives on a context whose grid is that
- * window.  n_host [W] (host): multiples of 64, 2^a 3^b 5^c 7^d, in [128, n];
+ * window.  n_host [W] (host): multiples of 64, FFT lengths as for n, in [128, n];
  * cfg.n must be a multiple of 64.  Walkers are grouped by window length; the
  * first call with a new length allocates that length's FFT plan, PSD weights
  * and data window (kept until lisa_td_destroy).  Rewriting the order of

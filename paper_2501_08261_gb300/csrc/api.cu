@@ -217,7 +217,7 @@ static int create_ctx(lisa_td_ctx** out, const lisa_td_config* cfg,
   c->esize = cfg->precision == 0 ? 8 : 4;
   if (lisa::plan_fft(c->n, &c->plan) != 0) {
     free_ctx(c);
-    return fail(LISA_TD_EINVAL, "n must be 2^a 3^b 5^c 7^d");
+    return fail(LISA_TD_EINVAL, "n must be 2^a 3^b 5^c 7^d times at most one prime in [11, 127]");
   }
   const int64_t n = c->n;
   const size_t W = (size_t)c->wmax_pad;

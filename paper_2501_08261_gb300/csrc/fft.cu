@@ -10,7 +10,8 @@
 //           walkers separate as X = (Z_k + conj Z_{n-k})/2, Y = (Z_k - conj Z_{n-k})/2i,
 //           and the weighted |.|^2 of the band bins (k <= n/2) is summed.
 // The n1- and n2-point transforms are Stockham radix-2/3/4/5/7/8 stages in
-// shared memory, pairs of walkers along the fast axis.
+// shared memory, pairs of walkers along the fast axis, plus at most one stage
+// of a prime radix in [11, 127] evaluated as a direct DFT.
 #include <math.h>
 
 #include "internal.h"
@@ -184,6 +185,74 @@ __device__ void stage(const C* __restrict__ A, C* __restrict__ B, int m, int L, 
   }
 }
 
+// one stage of a prime radix R in [11, 127] (at most one per plan), in two
+// sweeps over shared memory:
+//  1. the stage twiddles in place, y_q = A_q W_m^{q k stride} (k = j mod L);
+//  2. the R-point DFT of y by conjugate pairs: with u_q = y_q + y_{R-q},
+//     v_q = y_q - y_{R-q} and W_R^{q s} = c + i d for q, s in [1, h], h = (R-1)/2,
+//       out_s     = y_0 + sum_q c u_q + i sum_q d v_q,
+//       out_{R-s} = y_0 + sum_q c u_q - i sum_q d v_q,
+//     and out_0 = y_0 + sum_q u_q (the s = 0 item, where W_R^0 = 1 and d = 0).
+// One thread per (column, j, s <= h): R/2 pair loads and 4 FMA per output
+// pair and q, with W_R^{q s} = W_m^{q s nb} read from the same table.
+template <typename C>
+__device__ void stage_prime(C* __restrict__ A, C* __restrict__ B, int m, int R, int L,
+                            unsigned magL, int lgP, const C* __restrict__ tw, int tid, int nth) {
+  const int nb = m / R;
+  const int stride = m / (L * R);
+  const int P = 1 << lgP;
+  // i / d as umulhi(i, 2^32 / d + 1), exact for i, d < 2^16 and d > 1
+  if (L > 1) {                                   // then nb >= L > 1
+    const unsigned mag_nb = 0xFFFFFFFFu / (unsigned)nb + 1u;
+    for (int item = tid; item < (m << lgP); item += nth) {
+      const int p = item & (P - 1), i = item >> lgP;   // i = j + q nb
+      const int q = (int)__umulhi((unsigned)i, mag_nb), j = i - q * nb;
+      const int k = j - (int)__umulhi((unsigned)j, magL) * L;
+      if (q > 0 && k > 0) A[item] = cmulv(A[item], tw[q * k * stride]);
+    }
+    __syncthreads();
+  }
+  const int h = (R - 1) / 2;
+  const int nsj = h + 1;
+  const unsigned mag_s = 0xFFFFFFFFu / (unsigned)nsj + 1u;
+  for (int item = tid; item < ((nb * nsj) << lgP); item += nth) {
+    const int p = item & (P - 1), js = item >> lgP;
+    const int j = (int)__umulhi((unsigned)js, mag_s), s = js - j * nsj;
+    const int jq = L == 1 ? j : (int)__umulhi((unsigned)j, magL);
+    const int k = j - jq * L;
+    const C* col = A + (size_t)j * P + p;
+    C U, V;
+    U.x = 0;
+    U.y = 0;
+    V.x = 0;
+    V.y = 0;
+    const int e = s * nb;                        // W_R^{q s} = tw[q e mod m]
+    int idx = 0;
+    for (int q = 1; q <= h; ++q) {
+      const C a = col[(size_t)q * nb * P];
+      const C b = col[(size_t)(R - q) * nb * P];
+      idx += e;
+      if (idx >= m) idx -= m;
+      const C w = tw[idx];
+      U.x += w.x * (a.x + b.x);
+      U.y += w.x * (a.y + b.y);
+      V.x += w.y * (a.x - b.x);
+      V.y += w.y * (a.y - b.y);
+    }
+    const int base = (j - k) * R + k;
+    const C y0 = col[0];
+    C o;
+    o.x = y0.x + U.x - V.y;
+    o.y = y0.y + U.y + V.x;
+    B[(size_t)(base + s * L) * P + p] = o;
+    if (s > 0) {
+      o.x = y0.x + U.x + V.y;
+      o.y = y0.y + U.y - V.x;
+      B[(size_t)(base + (R - s) * L) * P + p] = o;
+    }
+  }
+}
+
 // full m-point transform of 2^lgP columns; returns the buffer holding the result
 template <typename C>
 __device__ C* transform(C* buf0, C* buf1, int m, int lgP, const Radices& rd,
@@ -200,7 +269,8 @@ __device__ C* transform(C* buf0, C* buf1, int m, int lgP, const Radices& rd,
       case 4: stage<4>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
       case 5: stage<5>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
       case 7: stage<7>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
-      default: stage<8>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      case 8: stage<8>(A, B, m, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
+      default: stage_prime(A, B, m, r, L, mag, lgP, tw, threadIdx.x, blockDim.x); break;
     }
     __syncthreads();
     C* t = A;
@@ -438,6 +508,7 @@ void radices_of(int m, Radices* rd) {
   while (m % 3 == 0) { rd->r[rd->nr++] = 3; m /= 3; }
   while (m % 5 == 0) { rd->r[rd->nr++] = 5; m /= 5; }
   while (m % 7 == 0) { rd->r[rd->nr++] = 7; m /= 7; }
+  if (m > 1) rd->r[rd->nr++] = m;                  // the one prime factor in [11, 127]
 }
 
 template <typename R>
@@ -503,7 +574,12 @@ int plan_fft(int64_t n, FftPlan* p) {
   int64_t m = n;
   for (int f : {2, 3, 5, 7})
     while (m % f == 0) m /= f;
-  if (m != 1 || n < 4) return -1;
+  // besides 2, 3, 5, 7 at most one prime factor, in [11, 127] (the 61-day
+  // window at 5 s is 2^7 3^3 5 61)
+  bool prime = m >= 11 && m <= 127;
+  for (int64_t d = 2; prime && d * d <= m; ++d)
+    if (m % d == 0) prime = false;
+  if ((m != 1 && !prime) || n < 4) return -1;
   int64_t best = 1;
   for (int64_t d = 1; d * d <= n; ++d)
     if (n % d == 0) best = d;

@@ -77,7 +77,7 @@ extern "C" int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const
   c.n = cfg->n;
   c.wmax_pad = W;
   c.esize = cfg->precision == 0 ? 8 : 4;
-  if (plan_fft(c.n, &c.plan) != 0) return report_error(LISA_TD_EINVAL, "noalloc: n must be 2^a 3^b 5^c 7^d");
+  if (plan_fft(c.n, &c.plan) != 0) return report_error(LISA_TD_EINVAL, "noalloc: n must be 2^a 3^b 5^c 7^d times at most one prime in [11, 127]");
   const int64_t n = c.n;
   const size_t cs = 2 * (size_t)c.esize;
   // scratch layout, each region 256-byte aligned

@@ -277,7 +277,7 @@ int lisa_td_loglike_ragged(lisa_td_ctx* c, const double* params_dev, int32_t W,
     FftPlan p;
     if (nv < 2 * kTdiTile || nv > c->n || nv % kTdiTile || plan_fft(nv, &p) != 0)
       return report_error(LISA_TD_EINVAL,
-                          "n[%d]=%lld: window lengths must be multiples of %d, 2^a 3^b 5^c 7^d, "
+                          "n[%d]=%lld: window lengths must be multiples of %d, 2^a 3^b 5^c 7^d (times at most one prime in [11, 127]), "
                           "in [%d, n]", w, (long long)nv, kTdiTile, 2 * kTdiTile);
     cls[nv].push_back(w);
   }

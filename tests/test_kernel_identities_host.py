@@ -184,3 +184,71 @@ def test_combined_pair_fir_equals_the_sum_of_its_terms():
             c = s + b
             want += sg * float(np.dot(w, y[c - H:c - H + K]))
         assert abs(got - want) <= 1e-12, (s, got, want)
+
+
+def _prime_stage(A, R, L, tw):
+    """fft.cu's prime-radix stage: the stage twiddles in place, then the R-point
+    DFT by conjugate pairs u_q = y_q + y_{R-q}, v_q = y_q - y_{R-q}."""
+    m = A.size
+    nb, stride = m // R, m // (L * R)
+    y = A.copy()
+    for i in range(m):
+        q, j = divmod(i, nb)
+        k = j % L
+        if q > 0 and k > 0:
+            y[i] *= tw[q * k * stride]
+    B = np.zeros(m, dtype=np.complex128)
+    h = (R - 1) // 2
+    for j in range(nb):
+        k = j % L
+        base = (j - k) * R + k
+        for s in range(h + 1):
+            U = V = 0j
+            for q in range(1, h + 1):
+                a, b = y[j + q * nb], y[j + (R - q) * nb]
+                w = tw[(q * s * nb) % m]
+                U += w.real * (a + b)
+                V += w.imag * (a - b)
+            B[base + s * L] = y[j] + U + 1j * V
+            if s > 0:
+                B[base + (R - s) * L] = y[j] + U - 1j * V
+    return B
+
+
+def _stockham(x, radices):
+    """The pass kernels' Stockham stages in numpy: stage (R, L) reads
+    A[j + q nb], applies W_m^{q (k stride + s nb)} (k = j mod L: the stage
+    twiddle times W_R^{q s}) and writes B[(j - k) R + k + s L]; a prime radix
+    R >= 11 goes through _prime_stage."""
+    m = x.size
+    tw = np.exp(-2j * np.pi * np.arange(m) / m)
+    A = x.astype(np.complex128)
+    L = 1
+    for R in radices:
+        if R >= 11:
+            A = _prime_stage(A, R, L, tw)
+            L *= R
+            continue
+        nb, stride = m // R, m // (L * R)
+        B = np.zeros(m, dtype=np.complex128)
+        for j in range(nb):
+            k = j % L
+            base = (j - k) * R + k
+            for s in range(R):
+                e = k * stride + s * nb
+                q = np.arange(R)
+                B[base + s * L] = np.sum(A[j + q * nb] * tw[(q * e) % m])
+        A = B
+        L *= R
+    return A
+
+
+@pytest.mark.parametrize("radices", [(8, 3, 5), (61,), (2, 61), (61, 3, 2), (4, 2, 3, 61),
+                                     (8, 2, 61), (11,), (3, 127)])
+def test_stockham_stages_with_a_prime_radix_are_the_dft(radices):
+    """The stage order and twiddle indices of fft.cu, including the direct
+    prime-radix stage that lengths with a factor in [11, 127] use (the 61-day
+    window at 5 s), against numpy's FFT."""
+    m = int(np.prod(radices))
+    x = np.random.default_rng(m).standard_normal(m) + 1j * np.random.default_rng(m + 1).standard_normal(m)
+    assert np.max(np.abs(_stockham(x, radices) - np.fft.fft(x))) <= 1e-12 * np.sqrt(m) * np.max(np.abs(x)) * m
