@@ -42,6 +42,22 @@ def test_rejects_sizes_beyond_the_static_scratch():
         assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(ok), fake, 78, fake, None) == -3
 
 
+def test_grid_length_rule():
+    """FFT lengths: 2^a 3^b 5^c 7^d times at most one prime in [11, 127].  The
+    plan is checked before any CUDA call, so no GPU is needed for the refusals."""
+    lib = api.load_library(api._build.build())
+    fake = ctypes.c_void_p(1 << 20)                   # never dereferenced
+    for n in (64 * 11 * 13, 64 * 131, 64 * 61 * 61, 17280 * 11 * 11):
+        cfg = api.make_config(dt=5.0, n=n, precision=1)
+        assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(cfg), fake, 2, fake, None) == -1, n
+        assert b"prime" in lib.lisa_td_last_error() or b"2^" in lib.lisa_td_last_error(), n
+    if not torch.cuda.is_available():
+        # accepted lengths pass the plan and stop at the first CUDA call
+        for n in (64 * 61, 64 * 11, 64 * 127, 2 ** 6 * 3 ** 3 * 5 * 61):
+            cfg = api.make_config(dt=5.0, n=n, precision=1)
+            assert lib.lisa_td_residual_loglike_noalloc(ctypes.byref(cfg), fake, 2, fake, None) == -3, n
+
+
 def _walkers(cfg, w, seed):
     return workloads.prior_draws(w, cfg["n"], cfg["dt"], seed, logm=(5.5, 7.0))
 
@@ -93,6 +109,21 @@ def test_residual_norm_at_radix7_lengths_matches_oracle(n, precision):
     likelihood on the same residual.  The mixed path gets the oracle's
     residual rounded to FP32, so only its FFT and norm arithmetic is compared:
     a relative bar of 2e-5 on a sum of ~n/10 positive terms."""
+    _norm_case(n, precision)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [3904, 8128, 2112, 40640])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_residual_norm_at_prime_factor_lengths_matches_oracle(n, precision):
+    """As above, at lengths with one prime factor in [11, 127], whose plans
+    end a pass with the direct prime-radix stage: n1 = 61 (odd, the stage
+    alone), n2 = 127, n1 = 44 = 4 x 11 and n2 = 254 = 2 x 127 (the stage
+    after others, with its twiddle sweep)."""
+    _norm_case(n, precision)
+
+
+def _norm_case(n, precision):
     from oracle import likelihood
     from paper_2501_08261_gb300 import build
     build.build()
