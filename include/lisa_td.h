@@ -270,7 +270,8 @@ int lisa_td_residual_loglike_noalloc(const lisa_td_config* cfg, const void* r_de
  * int64 sample indices rising strictly from 0 to n - 1, B >= 4).  Computes
  * the fiducial's carriers, X0 and node values; replaces an earlier set-up.
  * Allocates n (76 + 24 nmodes) + 96 x 48 x max(B, 16384) + 48 nmodes B
- * + 3 nmodes B (16 or 8) max_walkers bytes (48 = the TDI-2 terms of X, Y, Z,
+ * + 3 nmodes B (16 or 8) Wmax bytes, Wmax = max_walkers rounded up to a
+ * multiple of 32 (48 = the TDI-2 terms of X, Y, Z,
  * 24 for TDI 1.5; the last term is the node differences, 16 B per complex
  * value in FP64 contexts, 8 in mixed ones); synchronises `stream`.  The node
  * sums are FP64 in both precisions (FP32 terms would leave rounding that the
