@@ -132,3 +132,20 @@ def test_allocation_failure_injection_needs_no_gpu(libpath, monkeypatch):
     assert lib.lisa_td_create(ctypes.byref(h), ctypes.byref(cfg), None) == -2
     assert h.value is None
     assert b"cudaMalloc" in lib.lisa_td_last_error()
+
+
+def test_binding_refuses_truncated_or_mistyped_tensors():
+    """The C ABI takes bare pointers, so the binding checks every tensor before
+    its pointer crosses: truncated data ([3][n - 1] for [3][n]), another
+    dtype, host memory and non-contiguous views are refused on the host."""
+    torch = pytest.importorskip("torch")
+    n = 64
+    full = torch.zeros((3, n), dtype=torch.float64)
+    with pytest.raises(ValueError, match="shape"):
+        api._need(full[:, :-1], torch.float64, (3, n), "data")
+    with pytest.raises(ValueError, match="shape"):
+        api._need(full[:2], torch.float64, (3, n), "data")
+    with pytest.raises(TypeError, match="dtype"):
+        api._need(full.float(), torch.float64, (3, n), "data")
+    with pytest.raises(ValueError, match="CUDA"):
+        api._need(full, torch.float64, (3, n), "data")
