@@ -85,6 +85,49 @@ class MH:
     def set_flow_logq(self, flow):
         api.flow_logprob(flow, self.x, self.W, self.logq)
 
+    # checkpoint / resume: the likelihood holds no chain state, so a chain is
+    # its walkers' positions, logL and log q plus the device generator's state
+    def state(self):
+        """The chain's state as host arrays: positions, logL, log q, the last
+        acceptance flags, the walkers' inverse temperatures, the prior box and
+        the device generator's state.  Restoring it and repeating the same
+        steps gives the same chain bit for bit (every kernel of a step is
+        deterministic and the random numbers come from the restored generator)."""
+        self.torch.cuda.synchronize()
+        return {"x": self.x.cpu().numpy(), "logl": self.logl.cpu().numpy(),
+                "logq": self.logq.cpu().numpy(), "acc": self.acc.cpu().numpy(),
+                "beta": self._betas_host(), "lo": self.lo.copy(), "hi": self.hi.copy(),
+                "rng": self.gen.get_state().numpy()}
+
+    def restore(self, st):
+        """Load a state() of a chain with the same walker count, temperatures
+        and prior box; raises ValueError otherwise."""
+        torch = self.torch
+        x = np.asarray(st["x"], dtype=np.float64)
+        if x.shape != (self.W, 15):
+            raise ValueError(f"checkpoint holds {x.shape[0]} walkers, this chain {self.W}")
+        if not np.array_equal(np.asarray(st["beta"], dtype=np.float64), self._betas_host()):
+            raise ValueError("checkpoint was taken at other temperatures")
+        if not (np.array_equal(st["lo"], self.lo) and np.array_equal(st["hi"], self.hi)):
+            raise ValueError("checkpoint was taken with another prior box")
+        f64 = dict(dtype=torch.float64, device="cuda")
+        self.x.copy_(torch.as_tensor(x, **f64))
+        self.logl.copy_(torch.as_tensor(np.asarray(st["logl"], dtype=np.float64), **f64))
+        self.logq.copy_(torch.as_tensor(np.asarray(st["logq"], dtype=np.float64), **f64))
+        self.acc.copy_(torch.as_tensor(np.asarray(st["acc"], dtype=np.int32), device="cuda"))
+        self.gen.set_state(torch.as_tensor(np.ascontiguousarray(st["rng"], dtype=np.uint8)))
+
+    def save(self, path):
+        """state() to an .npz file."""
+        np.savez(path, **self.state())
+
+    def load(self, path):
+        with np.load(path) as f:
+            self.restore({k: f[k] for k in f.files})
+
+    def _betas_host(self):
+        return np.ones(self.W) if self.beta is None else self.beta.cpu().numpy()
+
     def run(self, step_fn, steps, record=None):
         """`steps` MH steps; returns (chain [steps][W][15] host array or None,
         mean acceptance, GPU milliseconds measured with CUDA events)."""
@@ -176,6 +219,17 @@ class PT(MH):
         acc = self._accept(self.lik.loglike(self.xp)).clone()
         self.swap()
         return acc
+
+    def state(self):
+        st = super().state()
+        st["swapped"] = self.swapped.cpu().numpy()
+        return st
+
+    def restore(self, st):
+        super().restore(st)
+        if "swapped" in st:
+            self.swapped.copy_(self.torch.as_tensor(np.asarray(st["swapped"], dtype=np.int32),
+                                                    device="cuda"))
 
     def swap(self):
         torch = self.torch

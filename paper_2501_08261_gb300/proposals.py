@@ -32,6 +32,33 @@ def flow_init(perms, D, L, H, seed):
     return np.concatenate(out).astype(np.float32)
 
 
+def flow_state(fl, D, layers, hidden, idx, perms, mu, scale):
+    """A trained flow as host arrays: its shape, coupling masks, frame (mu [15],
+    scale [D]: the library keeps them write-only, so the caller passes the ones
+    it set) and parameters from flow_get_params.  The optimiser's moments are
+    not kept: a restored flow proposes and scores; training starts afresh."""
+    import torch
+    params = torch.empty(api.flow_nparams(fl), dtype=torch.float32, device="cuda")
+    api.flow_get_params(fl, params)
+    torch.cuda.synchronize()
+    return {"D": np.int64(D), "layers": np.int64(layers), "hidden": np.int64(hidden),
+            "idx": np.asarray(idx, dtype=np.int32), "perms": np.asarray(perms, dtype=np.int32),
+            "mu": np.asarray(mu, dtype=np.float64), "scale": np.asarray(scale, dtype=np.float64),
+            "params": params.cpu().numpy()}
+
+
+def flow_from_state(st, max_batch):
+    """A new flow context from flow_state() (or the arrays of its .npz file)."""
+    import torch
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+    fl = api.flow_create(int(st["D"]), int(st["layers"]), int(st["hidden"]), max_batch,
+                         [int(i) for i in st["idx"]], np.asarray(st["perms"]))
+    api.flow_set_params(fl, torch.as_tensor(np.ascontiguousarray(st["params"], dtype=np.float32),
+                                            device="cuda"))
+    api.flow_set_frame(fl, T(st["mu"]), T(st["scale"]))
+    return fl
+
+
 def compare(cfg_name="c3_prec_1d", W=512, rw_steps=600, burn=100, steps=600, epochs=40,
             batch=4096, lr=1e-3, layers=6, seed=1):
     import torch
