@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -137,12 +138,17 @@ int check_orbit_table(const lisa_td_config* g, const lisa_td_orbit_table* T, dou
 
 namespace lisa {
 
+const char* const kStageRange[7] = {"lisa_td/prep", "lisa_td/waveform", "lisa_td/project",
+                                    "lisa_td/tdi", "lisa_td/fft_pass1", "lisa_td/fft_pass2_norm",
+                                    "lisa_td/reduce"};
+
 cudaError_t run_loglike_stages(const lisa_td_ctx* c, const double* params, int W, double* logl,
                                int32_t* status, cudaStream_t s, cudaEvent_t* ev) {
   const int Wp = pad32(W);
   cudaError_t e = cudaSuccess;
 #define STAGE(k, call)                                   \
   do {                                                   \
+    TraceRange range_(kStageRange[k]);                   \
     if (ev && (e = cudaEventRecord(ev[k], s)) != cudaSuccess) return e; \
     if ((e = (call)) != cudaSuccess) return e;           \
   } while (0)

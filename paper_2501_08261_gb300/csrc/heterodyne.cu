@@ -20,6 +20,7 @@
 
 #include "delay.cuh"
 #include "internal.h"
+#include "trace.h"
 #include "standin.cuh"
 
 namespace lisa {
@@ -820,6 +821,13 @@ cudaError_t run_nodes(lisa_td_ctx* c, HetState* h, const double* params, int W, 
 
 }  // namespace lisa
 
+namespace lisa {
+const char* const kHetStageRange[7] = {"lisa_td_het/prep", "lisa_td_het/nodes",
+                                       "lisa_td_het/expand", "lisa_td_het/empty",
+                                       "lisa_td_het/fft_pass1", "lisa_td_het/fft_pass2_norm",
+                                       "lisa_td_het/reduce"};
+}  // namespace lisa
+
 extern "C" {
 
 int lisa_td_het_setup(lisa_td_ctx* c, const double* theta0_host, const int64_t* nodes_host,
@@ -961,6 +969,7 @@ int lisa_td_het_loglike(lisa_td_ctx* c, const double* params_dev, int32_t W, dou
   cudaError_t e = refresh_base(c, h, s);
 #define STAGE(k, call)                                                   \
   do {                                                                   \
+    TraceRange range_(kHetStageRange[k]);                                \
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[k], s);           \
     if (e == cudaSuccess) e = (call);                                    \
   } while (0)

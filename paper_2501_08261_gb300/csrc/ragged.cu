@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "trace.h"
 
 namespace lisa {
 namespace {
@@ -412,6 +413,7 @@ int lisa_td_loglike_ragged(lisa_td_ctx* c, const double* params_dev, int32_t W,
     }
     r->key = key;
   }
+  lisa::TraceRange range_("lisa_td/ragged_graph");
   e = cudaGraphLaunch(r->exec, s);
   return e == cudaSuccess ? LISA_TD_OK : report_error(LISA_TD_ECUDA, "ragged graph launch: %s", cudaGetErrorString(e));
 }
