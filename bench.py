@@ -531,8 +531,12 @@ def run_ours(args):
                 "peak_measured_note": "lisa_td_fp32_fma_rate: 16 independent FMA chains per "
                                       "thread, 2048 threads per SM, best of 3, measured before "
                                       "the timed region"}
+    # the headline metric's name, or the same metric named for another grid / batch
+    metric = METRIC if (cfg["n"] == 1036800 and cfg["dt"] == 5.0 and W == WALKERS) else (
+        f"logL evals/s ({cfg['n'] * cfg['dt'] / 86400:g} d @{cfg['dt']:g} s, {W} walkers): "
+        "mixed vs FP64 path at |dlogL|<=0.05")
     out = {
-        "metric": METRIC, "value": round(value, 2), "unit": "logL evals/s", "n_gpus": ws,
+        "metric": metric, "value": round(value, 2), "unit": "logL evals/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms32 / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+df32",
         "data": "synthetic (seeded prior draws; zero-noise injection)",
