@@ -55,7 +55,7 @@ def test_light_time_solves_light_cone_equation():
 
 
 # -------------------------------------------------------------------- DFT --
-@pytest.mark.parametrize("n", [60, 120, 840, 17280])
+@pytest.mark.parametrize("n", [60, 120, 840, 17280, 244, 3904, 19520])   # 244, 3904, 19520: the factor 61 of the 61-day grid
 def test_fft_matches_bruteforce_dft(n):
     rng = np.random.default_rng(n)
     a = rng.normal(size=n)
