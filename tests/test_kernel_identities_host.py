@@ -252,3 +252,46 @@ def test_stockham_stages_with_a_prime_radix_are_the_dft(radices):
     m = int(np.prod(radices))
     x = np.random.default_rng(m).standard_normal(m) + 1j * np.random.default_rng(m + 1).standard_normal(m)
     assert np.max(np.abs(_stockham(x, radices) - np.fft.fft(x))) <= 1e-12 * np.sqrt(m) * np.max(np.abs(x)) * m
+
+
+def _expand_weights_f32(xs, i):
+    """het_expand_kernel's FP32 cubic weights of sample i from node indices xs
+    [4], in the kernel's order: den_q = prod_{t != q} (x_q - x_t) over t
+    ascending, 1 / den_q, then (e1 e23) / den_0, (e0 e23) / den_1,
+    (e01 e3) / den_2, (e01 e2) / den_3 with e_q = i - x_q."""
+    f = np.float32
+    x = [f(v) for v in xs]
+    dinv = []
+    for q in range(4):
+        den = f(1)
+        for t in range(4):
+            if t != q:
+                den = f(den * f(x[q] - x[t]))
+        dinv.append(f(f(1) / den))
+    xi = f(i)
+    e = [f(xi - x[q]) for q in range(4)]
+    e01, e23 = f(e[0] * e[1]), f(e[2] * e[3])
+    return np.array([f(f(e[1] * e23) * dinv[0]), f(f(e[0] * e23) * dinv[1]),
+                     f(f(e01 * e[3]) * dinv[2]), f(f(e01 * e[2]) * dinv[3])], dtype=np.float64)
+
+
+@pytest.mark.parametrize("xs", [(0, 1, 2, 3), (0, 50, 100, 150), (1000, 1050, 5000, 13640),
+                                (20000, 28640, 37280, 45920), (5000, 13640, 13641, 13642)])
+def test_expansion_weights_in_fp32_stay_within_rounding(xs):
+    """The heterodyne expansion's Lagrange-form weights in FP32 (node indices
+    are exact integers below 2^24, so e_q and the node differences are exact):
+    every weight within a few FP32 roundings of the FP64 Lagrange weight, for
+    uniform spacing, the 250 s start taper, a taper-to-chirp step and the
+    12 h cap, and dense nodes after a long interval (weights up to ~1e3, a
+    spacing the node rule avoids: its chirp spacing has shrunk to about one
+    sample where the dense window starts)."""
+    xs64 = np.array(xs, dtype=np.float64)
+    for i in range(xs[0], xs[3] + 1, max(1, (xs[3] - xs[0]) // 997)):
+        w64 = np.array([np.prod([(i - xs64[t]) / (xs64[q] - xs64[t]) for t in range(4) if t != q])
+                        for q in range(4)])
+        w32 = _expand_weights_f32(xs, i)
+        # the cubic reproduces constants (to FP64 rounding of weights that
+        # reach ~1e3 where dense nodes follow a long interval)
+        assert abs(np.sum(w64) - 1.0) <= 1e-14 * np.sum(np.abs(w64))
+        # each weight is five or six correctly rounded FP32 operations on exact inputs
+        assert np.all(np.abs(w32 - w64) <= 8 * 2.0 ** -24 * np.abs(w64) + 1e-30), (i, w32, w64)
