@@ -394,7 +394,7 @@ def heterodyne_measure(torch, api, workloads, kw, cfg, params, nball, steps):
                                         "(the continuous-time response) as the reference"},
             "definition": "fiducial = the injection; nodes: every sample across the merger, "
                           "chirp-rate spacing (df 2e-5 Hz, <= 12 h) elsewhere, 250 s over the start "
-                          "taper; cubic interpolation between nodes; node sums FP64, expansion + FFT FP32; data = the fiducial's "
+                          "taper, adjacent spacings graded within a factor 4; cubic interpolation between nodes; node sums FP64, expansion + FFT FP32; data = the fiducial's "
                           "continuous-time response"}
 
 
