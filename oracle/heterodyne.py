@@ -48,7 +48,6 @@ the interpolation error of the sampled path: ~1e-13 of the signal where h is
 band-limited, but up to ~1e-4 within a few stencil widths of the stand-in's
 merger attachment, where h is only C1 (its second derivative jumps at t_m).
 """
-import math
 
 import numpy as np
 

@@ -248,7 +248,6 @@ def test_node_differences_on_an_orbit_table_match_oracle():
     """orbit_kind 2: the node geometry comes from the library's resampling of
     the caller's spacecraft positions, the oracle reads the same table through
     its own interpolation (FP64, one day, TDI 2)."""
-    import dataclasses
     from oracle import orbits
     from paper_2501_08261_gb300 import api
     t0_tab, dt_tab = -2 * 3600.0, 3600.0

@@ -5,13 +5,12 @@ the sampled (Lagrange) response of ``pipeline.aet``, the exactness of the
 construction at the fiducial and with a node at every sample, the
 fourth-order convergence of cubic interpolation, and the node rule's accuracy
 and spacing.  CPU only."""
-import math
 
 import numpy as np
 import pytest
 
 from oracle import heterodyne as H
-from oracle import likelihood, orbits, pipeline, waveform
+from oracle import likelihood, pipeline, waveform
 from paper_2501_08261_gb300 import workloads as wl
 
 DAY = 86400.0

@@ -4,7 +4,6 @@ distribution of the chain -- nothing here re-types the oracle's formulas."""
 import math
 
 import numpy as np
-import pytest
 from scipy.stats import multivariate_normal
 
 from oracle import likelihood, pipeline, sampler
