@@ -171,6 +171,49 @@ def test_interpolation_error_is_fourth_order_in_the_node_spacing():
     assert 9.0 <= err[0] / err[1] <= 24.0 and 9.0 <= err[1] / err[2] <= 24.0, err
 
 
+def test_expansion_is_exact_for_cubic_envelopes_and_checks_its_nodes():
+    """Step 5 on its own.  Node differences sampled from a complex cubic in the
+    sample index expand to that cubic times the carrier at every sample, for
+    any node spacing (wrong Lagrange weights fail this).  For a quartic the
+    result is, sample by sample, numpy's degree-3 polyfit through the four
+    nodes a .. a + 3, a = min(max(b - 1, 0), B - 4) around the sample's
+    interval b (a shifted stencil fails this).  The node list is checked."""
+    s = _setup(n=400)
+    th0 = _theta()
+    nodes = np.array([0, 3, 10, 11, 40, 100, 101, 250, 399])
+    B = nodes.size
+    rng = np.random.default_rng(4)
+    coef = rng.normal(size=(5, 3, 5)) + 1j * rng.normal(size=(5, 3, 5))
+    i = np.arange(s.n)
+    c = H.carriers(th0, s, pipeline.grid(s))
+    x0 = np.zeros((3, s.n))
+    cubic = lambda x: sum(coef[..., k, None] * (x / 400.0) ** k for k in range(4))
+    out = H.expand(cubic(nodes), th0, s, nodes, x0)
+    want = np.stack([sum((c[j] * cubic(i)[j, ch]).real for j in range(5)) for ch in range(3)])
+    assert np.max(np.abs(out - want)) <= 1e-12 * np.max(np.abs(want))
+    quartic = lambda x: sum(coef[..., k, None] * (x / 400.0) ** k for k in range(5))
+    zq = quartic(nodes)
+    out = H.expand(zq, th0, s, nodes, x0)
+    env = np.zeros((5, 3, s.n), dtype=complex)
+    for k in range(s.n):
+        b = min(np.searchsorted(nodes, k, side="right") - 1, B - 2)
+        a = min(max(b - 1, 0), B - 4)
+        xs = nodes[a:a + 4] / 400.0
+        for j in range(5):
+            for ch in range(3):
+                env[j, ch, k] = (np.polyval(np.polyfit(xs, zq[j, ch, a:a + 4].real, 3), k / 400.0)
+                                 + 1j * np.polyval(np.polyfit(xs, zq[j, ch, a:a + 4].imag, 3),
+                                                   k / 400.0))
+    want = np.stack([sum((c[j] * env[j, ch]).real for j in range(5)) for ch in range(3)])
+    truth = np.stack([sum((c[j] * quartic(i)[j, ch]).real for j in range(5)) for ch in range(3)])
+    assert np.max(np.abs(out - want)) <= 1e-9 * np.max(np.abs(want))
+    assert np.max(np.abs(out - truth)) >= 1e-4 * np.max(np.abs(truth))   # not the quartic
+    dz = np.zeros((5, 3, 4), dtype=complex)
+    for bad in ([0, 5, 399], [1, 5, 9, 399], [0, 5, 9, 398], [0, 9, 5, 399]):
+        with pytest.raises(ValueError):
+            H.expand(dz[..., :len(bad)], th0, s, bad, x0)
+
+
 def test_node_rule_reaches_the_continuous_likelihood(aligned_day):
     """The node rule at a posterior-width offset (SNR ~ 1.2e3): the heterodyned
     logL within 0.01 of the continuous-time logL, and a coarser rule errs
