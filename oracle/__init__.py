@@ -29,6 +29,14 @@ Module map (paper section / equation each follows):
                  the paper names in Sec. I and Sec. IV, defined in the module):
                  analytic mode polarisations, the continuous-time response at
                  nodes, fiducial carriers and the interpolated model.
+* ``sampler``    Fisher matrix by central differences of logL, the
+                 Fisher-Gaussian proposal, the Metropolis-Hastings step and
+                 tempered replica exchange (Sec. II.C).
+* ``flow``       the affine-coupling flow of the learned proposal (forward,
+                 inverse, log q, gradients, Adam), with the kernels' bf16
+                 operand rounding as an option.
+* ``noise``      coloured Gaussian noise with the likelihood's PSDs (the
+                 signal-plus-noise data of the paper's next step, Sec. IV).
 
 Parity status: everything here is pinned by ``tests/test_oracle_*.py`` to
 closed forms, invariants, brute force or special cases, EXCEPT the absolute
